@@ -1,0 +1,435 @@
+"""Benchmark of the ALTO hot path on GB300.
+
+One step = the whole hot path over one synthetic tensor: ALTO generation
+(linearization, ordering, value permutation, partitioning, intervals, stats,
+flags) followed by the configuration's CP-ALS iterations, each an all-mode
+MTTKRP sweep plus the per-mode CP-ALS update.  The headline value is the
+all-mode MTTKRP nonzero throughput of that whole job,
+    value = iters * N * nnz / step time   [Gnnz/s],
+with the inputs resident in HBM when the timed region starts.  The MTTKRP
+kernels alone are also timed (CUDA events recorded by the library around
+every MTTKRP launch inside the timed steps) and reported against the HBM
+roofline of their compulsory bytes.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own replica of the workload (weak
+scaling; the path needs no exchange between GPUs); rank 0 prints the line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "all-mode MTTKRP Gnnz/s + % HBM roofline; CP-ALS s/iter vs plain FP32"
+DEFAULT_CONFIG = "zipf3d-4Mx4Mx30k"
+FALLBACK_HBM_GBS = 6800.0
+CPU_SAMPLE_NNZ = 20_000_000      # oracle CPU-baseline sample (about 15-20 s)
+REF_STEP_NNZ = 4_000_000         # reference-arm step sample
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default=DEFAULT_CONFIG)
+    p.add_argument("--fdtype", default=None, choices=[None, "f32", "bf16", "f64"])
+    p.add_argument("--variant", type=int, default=0, help="force one MTTKRP variant for every mode")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, replicas)
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mttkrp_kernels.cuh", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f64.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2102_10245_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(config, fdtype):
+    """DRAM bytes per MTTKRP launch from a committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "mttkrp_dram_traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get("%s/%s" % (config, fdtype))
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def mttkrp_bytes(nnz, key_bytes, val_bytes, distinct, R, fbytes, obytes, n):
+    """Compulsory bytes of one mode-n MTTKRP: the key and value stream, every
+    distinct input-factor row once and every distinct output row once."""
+    N = len(distinct)
+    b = nnz * (key_bytes + val_bytes)
+    b += sum(distinct[m] * R * fbytes for m in range(N) if m != n)
+    b += distinct[n] * R * obytes
+    return b
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and reference arm)
+
+def oracle_sweep_time(dims, idx, vals, U64, nnz_sample):
+    import oracle
+    sidx = [a[:nnz_sample] for a in idx]
+    sv = np.asarray(vals[:nnz_sample], dtype=np.float64)
+    t0 = time.perf_counter()
+    for n in range(len(dims)):
+        oracle.mttkrp(dims, sidx, sv, U64, n)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = synth.CONFIGS[args.config]
+    dims, idx, vals = synth.tensor(cfg)
+    U64 = [u.astype(np.float64) for u in synth.factors(cfg)]
+    S = min(REF_STEP_NNZ, len(vals))
+    N = len(dims)
+    for _ in range(args.warmup):
+        oracle_sweep_time(dims, idx, vals, U64, S)
+    ts = [oracle_sweep_time(dims, idx, vals, U64, S) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    value = N * S / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.config, "dims": list(dims), "nnz": len(vals), "rank": cfg["rank"],
+                   "sample_nnz": S, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+                         "sample": "all-mode FP64 COO MTTKRP over the first %d of %d nonzeros per step"
+                                   % (S, len(vals))},
+        "e2e": {"value": value, "unit": "Gnnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world, local):
+    from paper_2102_10245_gb300 import AltoTensor, launch_count, torch_allocator
+    import paper_2102_10245_gb300.build as lb
+    lb.build()
+
+    cfg = synth.CONFIGS[args.config]
+    fdtype = args.fdtype or cfg["fdtype"]
+    dims, idx, vals = synth.tensor(cfg)
+    U0 = synth.factors(cfg)
+    N, M, R, iters = len(dims), len(vals), cfg["rank"], cfg["iters"]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[fdtype]
+    vdt = torch.float64 if fdtype == "f64" else torch.float32
+
+    # CPU baseline first (rank 0, single GPU only), before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        S = min(CPU_SAMPLE_NNZ, M)
+        U64 = [u.astype(np.float64) for u in U0]
+        t = oracle_sweep_time(dims, idx, vals, U64, S)
+        cpu = {"value": N * S / t / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
+               "sample": "all-mode FP64 COO MTTKRP (the oracle) over the first %d of %d nonzeros, "
+                         "single thread, %.1f s" % (S, M, t)}
+        del U64
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # inputs resident in HBM
+    idx_d = [torch.from_numpy(a.view(np.int32)).to(dev) for a in idx]
+    vals_d = torch.from_numpy(vals.astype(np.float64 if fdtype == "f64" else np.float32)).to(dev)
+    U0_d = [torch.from_numpy(u).to(dev).to(tdt) for u in U0]
+    Uw = [torch.empty_like(u) for u in U0_d]
+    lam = torch.empty(R, dtype=torch.float64, device=dev)
+    alloc = torch_allocator()
+    variants = [args.variant] * N if args.variant else None
+    stream = torch.cuda.current_stream()
+
+    stats = {}
+    prof_ms = np.zeros(N)
+    prof_calls = np.zeros(N, dtype=np.int64)
+    phase = []   # (create_start, create_end / cpals_start, cpals_end) events per timed step
+
+    def step(record):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)] if record else None
+        if record:
+            evs[0].record(stream)
+        at = AltoTensor(dims, idx_d, vals_d, allocator=alloc, variants=variants)
+        if record:
+            at.profile(True)
+        for w, u in zip(Uw, U0_d):
+            w.copy_(u)
+        if record:
+            evs[1].record(stream)
+        _, fits = at.cpals(Uw, iters, lam=lam)
+        if record:
+            evs[2].record(stream)
+            phase.append(evs)
+            ms, calls = at.profile_read()
+            prof_ms[:] += ms
+            prof_calls[:] += calls
+        if not stats:
+            stats.update(at.stats())
+            stats["key_words"] = at.layout()["key_words"]
+            stats["fits"] = fits
+        at.close()
+        return fits
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        step(False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        fits = step(True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - n0
+    clk = clocks.stop()
+    barrier(world)
+    create_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in phase)
+    cpals_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in phase)
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    units = sum_over_ranks(float(iters * N * M), world)
+    value = units / (ms_step / 1e3) / 1e9
+
+    # MTTKRP kernels against the HBM roofline
+    fb = {"f32": 4, "bf16": 2, "f64": 8}[fdtype]
+    ob = 8 if fdtype == "f64" else 4
+    vb = 8 if fdtype == "f64" else 4
+    kb = 8 * stats["key_words"]
+    per_mode_bytes = [mttkrp_bytes(M, kb, vb, stats["distinct"], R, fb, ob, n) for n in range(N)]
+    tot_bytes = sum(per_mode_bytes[n] * prof_calls[n] for n in range(N))
+    tot_ms = float(prof_ms.sum())
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
+    peak, peak_src = measured_peak()
+    sweep_ms = tot_ms / max(1, int(prof_calls.min()))
+    traffic = recorded_traffic(args.config, fdtype)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": "alto MTTKRP (all modes, incl. output zeroing)",
+                "bytes_per_launch": {str(n): int(per_mode_bytes[n]) for n in range(N)}}
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        idx_h = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in idx]
+        vals_h = vals_d.cpu().pin_memory()
+        U0_h = [u.cpu().pin_memory() for u in U0_d]
+        out_h = [torch.empty(u.shape, dtype=u.dtype).pin_memory() for u in U0_d]
+        lam_h = torch.empty(R, dtype=torch.float64).pin_memory()
+        h2d = sum(a.numel() * a.element_size() for a in idx_h) + vals_h.numel() * vals_h.element_size() \
+            + sum(u.numel() * u.element_size() for u in U0_h)
+        d2h = sum(u.numel() * u.element_size() for u in out_h) + R * 8 + iters * 8
+
+        def step_e2e():
+            at = AltoTensor(dims, idx_h, vals_h, allocator=alloc, variants=variants)
+            for w, u in zip(Uw, U0_h):
+                w.copy_(u, non_blocking=True)
+            _, f = at.cpals(Uw, iters, lam=lam)
+            for o, w in zip(out_h, Uw):
+                o.copy_(w, non_blocking=True)
+            lam_h.copy_(lam, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            at.close()
+            return f
+        step_e2e()
+        k2 = max(2, args.steps // 2)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k2):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / k2, world)
+        e2e = {"value": units / (ms_e2e / 1e3) / 1e9, "unit": "Gnnz/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "steps": k2}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": fdtype, "data": "synthetic",
+        "config": {"workload": args.config, "dims": list(dims), "nnz": M, "rank": R, "iters": iters,
+                   "step": "alto_create + %d CP-ALS iterations (all-mode MTTKRP + update)" % iters,
+                   "l2": "inputs larger than L2 (COO %.1f GB, ALTO stream %.1f GB)"
+                         % ((N * 4 + vb) * M / 1e9, (kb + vb) * M / 1e9),
+                   "variant": stats["variant"] if args.variant == 0 else [args.variant] * N},
+        "mttkrp": {"sweep_ms": sweep_ms, "gnnz_s": N * M / (sweep_ms / 1e3) / 1e9 if sweep_ms > 0 else None,
+                   "ms_per_mode": [float(prof_ms[n] / max(1, prof_calls[n])) for n in range(N)],
+                   "calls": [int(c) for c in prof_calls]},
+        "create_ms": create_ms,
+        "cpals_s_per_iter": cpals_ms / 1e3 / iters,
+        "fit_last": fits[-1] if fits else None,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

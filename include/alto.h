@@ -1,0 +1,253 @@
+/*
+ * alto.h -- C ABI of libalto, a GB300 (sm_103a) implementation of the ALTO
+ * sparse tensor format and of the MTTKRP / CP-ALS computations over it
+ * (Helal et al., "ALTO: Adaptive Linearized Storage of Sparse Tensors",
+ * ICS '21).
+ *
+ * Conventions shared by every entry point:
+ *   - Plain pointers and sizes only.  `stream` is a cudaStream_t passed as
+ *     void* (NULL = the legacy default stream).  Work is enqueued on that
+ *     stream and runs asynchronously unless the entry point says it syncs.
+ *   - Every function returns an alto_status; on failure alto_last_error()
+ *     returns a message for the calling thread.  No C++ exception crosses
+ *     the ABI.
+ *   - Mode numbers are 0-based (the paper counts modes from 1).
+ *   - Factor matrices are row-major I_m x R with leading dimension R.
+ *   - Device-side errors (an index >= I_n, a bounded wait that ran out) are
+ *     recorded in a status word owned by the tensor and reported by the next
+ *     call that synchronises (alto_create, alto_cpals, alto_check).
+ *   - The library owns every buffer it allocates and frees it in
+ *     alto_destroy; caller buffers are only read or written, never freed.
+ */
+#ifndef ALTO_H
+#define ALTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct alto_tensor_s *alto_t;
+
+typedef enum {
+    ALTO_OK = 0,
+    ALTO_EINVAL = 1,    /* bad argument (null pointer, bad mode, bad dtype) */
+    ALTO_ENOMEM = 2,    /* an allocation failed */
+    ALTO_ECUDA = 3,     /* a CUDA runtime call failed */
+    ALTO_ETIMEOUT = 4,  /* a bounded device wait ran out */
+    ALTO_EOVERFLOW = 5, /* sum of index bits above 128 */
+    ALTO_ENOTSPD = 6,   /* Cholesky factorisation of the Gram product failed */
+    ALTO_ERANGE = 7     /* an input index is >= its mode length */
+} alto_status;
+
+typedef enum {
+    ALTO_F64 = 0,
+    ALTO_F32 = 1,
+    ALTO_BF16 = 2
+} alto_dtype;
+
+/* Output-accumulation variants of MTTKRP (Alg. 2 and Sec. 3.3). */
+typedef enum {
+    ALTO_VAR_AUTO = 0,    /* the library's choice (Sec. 3.3 reuse rule) */
+    ALTO_VAR_ATOMIC = 1,  /* direct atomic update per nonzero (Alg. 2, ATOMIC) */
+    ALTO_VAR_WARPAGG = 2, /* warp-level pre-aggregation of equal output rows,
+                             then atomics */
+    ALTO_VAR_SMEM = 3,    /* per-segment Temp in shared memory sized by the
+                             segment's output interval (Alg. 2, Temp_l), then
+                             one atomic flush per touched row */
+    ALTO_VAR_TEMP = 4     /* per-segment Temp in device memory plus the
+                             pull-based reduction of Alg. 2 */
+} alto_variant;
+
+#define ALTO_MAX_MODES 8
+
+/*
+ * Creation options.  Zero-initialise, or call alto_options_init.
+ *   key_bits : 0 = smallest native word that holds the index (64 or 128,
+ *              Sec. 4.2.3); 64 or 128 forces a width (64 fails with
+ *              ALTO_EOVERFLOW when the index needs more bits).
+ *   nparts   : number L of equal-nnz line segments (Sec. 3.2); 0 = auto.
+ *   variant  : per-mode MTTKRP variant (alto_variant); 0 = auto.
+ *   use_flags: 1 = store boundary/internal helper flags in the unused key
+ *              bits for modes whose fiber reuse is at most 4 (Sec. 3.3).
+ *   alloc/free/ctx: optional device allocator; when alloc is NULL the
+ *              library uses cudaMalloc / cudaFree.  alloc returns NULL on
+ *              failure, which the library reports as ALTO_ENOMEM.
+ */
+typedef struct {
+    int key_bits;
+    int64_t nparts;
+    int variant[ALTO_MAX_MODES];
+    int use_flags;
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} alto_options;
+
+/* Fill *opt with the defaults (all automatic, flags on, cudaMalloc). */
+alto_status alto_options_init(alto_options *opt);
+
+/*
+ * alto_create -- build the ALTO tensor from a COO tensor (Sec. 3.1-3.2).
+ *
+ * Linearization (bit-level gather of every mode index into one key, bits
+ * assigned level by level from the LSB, shorter modes first inside a level;
+ * Sec. 3.1, Eq. 1), ordering (stable ascending sort of the keys), value
+ * permutation, equal-nnz partitioning into L line segments with their
+ * per-mode intervals T_l (Sec. 3.2), per-mode distinct-row counts and fiber
+ * reuse, and the helper flags (Sec. 3.3).
+ *
+ *   out      : receives the handle.
+ *   nmodes   : N, 1 <= N <= ALTO_MAX_MODES.
+ *   dims     : host array of N mode lengths, each in [1, 2^32].
+ *   nnz      : M >= 0 nonzeros (duplicates are kept as separate nonzeros).
+ *   idx      : host array of N pointers; idx[n] points to M mode-n indices
+ *              (0-based) of width idx_bytes (4: uint32, 8: int64).  Each
+ *              pointer may be device or host memory (detected); host data is
+ *              copied to the device first.
+ *   vals     : M values of type vdtype (ALTO_F64 or ALTO_F32), device or
+ *              host memory.
+ *   opt      : options, or NULL for the defaults.
+ * The inputs are read only and may be freed once the call returns.  The
+ * call synchronises `stream` at its end and returns ALTO_ERANGE when an
+ * index is out of range.
+ */
+alto_status alto_create(alto_t *out, int nmodes, const uint64_t *dims,
+                        int64_t nnz, const void *const *idx, int idx_bytes,
+                        const void *vals, alto_dtype vdtype,
+                        const alto_options *opt, void *stream);
+
+/*
+ * alto_mttkrp -- mode-`mode` MTTKRP over the ALTO tensor (Sec. 2.2,
+ * Alg. 1-2): out[i_n][r] = sum_x v_x * prod_{m != n} U_m[i_m][r].
+ *
+ *   factors : host array of N device pointers, factors[m] an I_m x rank
+ *             matrix of fdtype; factors[mode] is not read (may be NULL).
+ *   fdtype  : ALTO_F64 (values must be F64), ALTO_F32 or ALTO_BF16 (values
+ *             must be F32; accumulation in FP32).
+ *   out     : device I_mode x rank matrix, FP64 when fdtype is ALTO_F64 and
+ *             FP32 otherwise; overwritten (the zero initialisation that
+ *             Alg. 2 leaves implicit is done here).
+ * Asynchronous on `stream`.  Scratch memory (Temp buffers of the
+ * ALTO_VAR_TEMP variant) is allocated on first use and kept in the handle.
+ */
+alto_status alto_mttkrp(alto_t t, int mode, const void *const *factors,
+                        int rank, alto_dtype fdtype, void *out, void *stream);
+
+/*
+ * alto_cpals -- `iters` iterations of CP-ALS (Sec. 2.2) with ALTO MTTKRP.
+ * Per mode n: M_n = MTTKRP_n; V = Hadamard product of U_m^T U_m over
+ * m != n (FP64); U_n = M_n V^{-1} through a Cholesky factorisation of V in
+ * FP64 (for FP32/BF16 factors the FP64 inverse is rounded to FP32 and
+ * applied with FP32 arithmetic); columns normalised by their 2-norm in the
+ * first iteration and by max(1, max |.|) afterwards, the norms going to
+ * lambda; U_n^T U_n recomputed (FP64).  The fit after each iteration is
+ * 1 - ||X - [[lambda; U]]|| / ||X||.
+ *
+ *   factors : host array of N device pointers to I_m x rank matrices of
+ *             fdtype: the initial factors on entry, the result on return.
+ *   lambda  : device array of rank doubles (output).
+ *   fit     : host array of `iters` doubles (output), or NULL.
+ * Synchronises `stream` at its end when fit is not NULL.
+ */
+alto_status alto_cpals(alto_t t, int rank, int iters, void *const *factors,
+                       alto_dtype fdtype, double *lambda, double *fit,
+                       void *stream);
+
+/*
+ * alto_get_layout -- the index layout (Sec. 3.1).  Any output may be NULL.
+ *   nmodes        : N.
+ *   bits_per_mode : N entries, ceil(log2 I_n).
+ *   masks         : N x 2 words (lo, hi): key bits that hold mode n.
+ *   key_words     : 1 (64-bit keys) or 2 (128-bit keys).
+ *   flag_bit      : N entries, the key bit of mode n's helper flag or -1.
+ */
+alto_status alto_get_layout(alto_t t, int *nmodes, int *bits_per_mode,
+                            uint64_t *masks, int *key_words, int *flag_bit);
+
+/*
+ * alto_get_stats -- plan statistics (Sec. 3.2-3.3).  Any output may be NULL.
+ *   nnz, nparts : M and L.
+ *   distinct    : N entries, number of distinct mode-n indices D_n.
+ *   reuse       : N entries, fiber reuse M / I_n.
+ *   variant     : N entries, the MTTKRP variant the plan uses per mode.
+ *   max_interval: N entries, the widest segment interval per mode.
+ */
+alto_status alto_get_stats(alto_t t, int64_t *nnz, int64_t *nparts,
+                           uint64_t *distinct, double *reuse, int *variant,
+                           uint64_t *max_interval);
+
+/*
+ * alto_export -- copy the format to HOST buffers (synchronises).  Any
+ * output may be NULL.
+ *   keys      : M x key_words uint64 (lo word first), ALTO order, with the
+ *               flag bits included.
+ *   perm      : M uint32, input position of each nonzero in ALTO order.
+ *   vals      : M values of the tensor's value dtype, ALTO order.
+ *   bounds    : L+1 segment boundaries.
+ *   intervals : L x N x 2 uint32, [start, end] of every segment and mode.
+ */
+alto_status alto_export(alto_t t, uint64_t *keys, uint32_t *perm, void *vals,
+                        int64_t *bounds, uint32_t *intervals);
+
+/* alto_set_variant -- override the MTTKRP variant of one mode. */
+alto_status alto_set_variant(alto_t t, int mode, int variant);
+
+/* alto_check -- synchronise `stream` and report a recorded device error. */
+alto_status alto_check(alto_t t, void *stream);
+
+/*
+ * alto_layout_for_dims -- the index layout of Sec. 3.1 for given mode
+ * lengths, computed on the host (no GPU needed).  Any output may be NULL.
+ *   bits_per_mode : N entries; masks : N x 2 words (lo, hi);
+ *   key_words     : 1 or 2; total_bits : sum of bits_per_mode (Eq. 1).
+ * Errors: ALTO_EINVAL (bad N or length), ALTO_EOVERFLOW (above 128 bits or
+ * above a forced 64-bit key).
+ */
+alto_status alto_layout_for_dims(int nmodes, const uint64_t *dims,
+                                 int key_bits, int *bits_per_mode,
+                                 uint64_t *masks, int *key_words,
+                                 int *total_bits);
+
+/*
+ * alto_decode_host -- de-linearization (EXTRACT of Alg. 1) on the host with
+ * the same precomputed masks the kernels use.  keys: count x key_words
+ * uint64 (lo word first; flag bits are ignored); idx: count x N uint32
+ * output (row-major).  Host memory only.
+ */
+alto_status alto_decode_host(int nmodes, const uint64_t *dims, int key_bits,
+                             int64_t count, const uint64_t *keys,
+                             uint32_t *idx);
+
+/*
+ * alto_profile -- enable (1) or disable (0) CUDA-event timing of this
+ * handle's MTTKRP launches (output zeroing, the kernel and, for the Temp
+ * variant, the pull pass), recorded on the launching stream.  Adds two event
+ * records per MTTKRP call; off by default.
+ */
+alto_status alto_profile(alto_t t, int enable);
+
+/*
+ * alto_profile_read -- synchronise the recorded events and return, per mode,
+ * the summed milliseconds (ms[N]) and number of timed MTTKRP calls
+ * (calls[N]) since the previous read; then reset.  Either output may be NULL.
+ */
+alto_status alto_profile_read(alto_t t, double *ms, int64_t *calls);
+
+/* alto_launch_count -- number of kernels the library has launched in this
+ * process so far (all handles). */
+alto_status alto_launch_count(uint64_t *count);
+
+/* alto_destroy -- free everything the handle owns.  NULL is accepted. */
+alto_status alto_destroy(alto_t t);
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char *alto_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALTO_H */

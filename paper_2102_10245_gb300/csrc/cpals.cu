@@ -1,0 +1,458 @@
+// CP-ALS driver over ALTO MTTKRP (Sec. 2.2).  Per mode n:
+//   M_n = MTTKRP_n                                   (mttkrp kernels)
+//   V   = Hadamard product of G_m = U_m^T U_m, m != n (FP64, one block)
+//   V = L L^T (Cholesky, FP64), V^{-1} = L^{-T} L^{-1} (FP64)
+//   A   = M_n V^{-1}      per row; FP64 for FP64 factors, otherwise the FP64
+//                         inverse rounded to FP32 and applied in FP32
+//   lambda_r = ||A_:r||_2 (first iteration) or max(1, max_i |A_ir|)
+//   U_n = A / lambda (stored in the factor dtype), G_n = U_n^T U_n (FP64 sums
+//         of FP32 partials)
+// and after the last mode the fit 1 - ||X - model|| / ||X|| from ||X||^2,
+// lambda^T (Hadamard of all G) lambda and <X, model> = sum_r lambda_r
+// sum_i U_N[i,r] M_N[i,r].
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace alto {
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kMaxR = 64;
+constexpr int kGramRows = 64;
+
+template <typename FT>
+struct CT {
+  using type = float;
+};
+template <>
+struct CT<double> {
+  using type = double;
+};
+
+template <typename FT>
+__device__ __forceinline__ typename CT<FT>::type to_ct(FT v) {
+  return static_cast<typename CT<FT>::type>(v);
+}
+template <>
+__device__ __forceinline__ float to_ct<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+template <typename FT>
+__device__ __forceinline__ FT from_float(float v);
+template <>
+__device__ __forceinline__ float from_float<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+// Accumulate the Gram contribution of one staged tile (rows x R, computing
+// type C) into per-thread partials: thread t owns entries t, t+256, ...
+template <typename C>
+__device__ __forceinline__ void gram_tile(const C (*tile)[kMaxR], int R, C* part) {
+  const int RR = R * R;
+#pragma unroll
+  for (int q = 0; q < kMaxR * kMaxR / kT; ++q) {
+    const int e = threadIdx.x + q * kT;
+    if (e < RR) {
+      const int a = e / R, b = e - a * R;
+      C s = C(0);
+#pragma unroll 8
+      for (int r = 0; r < kGramRows; ++r) s += tile[r][a] * tile[r][b];
+      part[q] += s;
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void gram_flush(const C* part, double* acc, int R) {
+  const int RR = R * R;
+#pragma unroll
+  for (int q = 0; q < kMaxR * kMaxR / kT; ++q)
+    if (threadIdx.x + q * kT < RR) acc[q] += static_cast<double>(part[q]);
+}
+
+// G += A^T A for A (I x R) of type FT.
+template <typename FT>
+__global__ void __launch_bounds__(kT) gram_kernel(const FT* __restrict__ A, int64_t I, int R,
+                                                  double* __restrict__ G) {
+  using C = typename CT<FT>::type;
+  __shared__ C tile[kGramRows][kMaxR];
+  constexpr int Q = kMaxR * kMaxR / kT;
+  C part[Q];
+  double acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    part[q] = C(0);
+    acc[q] = 0.0;
+  }
+  int since = 0;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * kGramRows; r0 < I;
+       r0 += static_cast<int64_t>(gridDim.x) * kGramRows) {
+    const int64_t rows = I - r0 < kGramRows ? I - r0 : kGramRows;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kGramRows * R; i += kT) {
+      const int rr = i / R, cc = i - rr * R;
+      tile[rr][cc] = rr < rows ? to_ct<FT>(A[(r0 + rr) * R + cc]) : C(0);
+    }
+    __syncthreads();
+    gram_tile<C>(tile, R, part);
+    if (++since == 16) {
+      gram_flush<C>(part, acc, R);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) part[q] = C(0);
+      since = 0;
+    }
+  }
+  gram_flush<C>(part, acc, R);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = threadIdx.x + q * kT;
+    if (e < R * R) atomicAdd(G + e, acc[q]);
+  }
+}
+
+// V = Hadamard of G_m (m != skip); Cholesky; V^{-1}.  One block.
+__global__ void __launch_bounds__(kT) chol_inv_kernel(const double* __restrict__ G, int N, int skip, int R,
+                                                      double* __restrict__ vinv64,
+                                                      float* __restrict__ vinv32, int* status) {
+  __shared__ double V[kMaxR * kMaxR];
+  __shared__ double Li[kMaxR * kMaxR];
+  __shared__ int bad;
+  const int RR = R * R;
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < RR; e += kT) {
+    double v = 1.0;
+    for (int m = 0; m < N; ++m)
+      if (m != skip) v *= G[static_cast<size_t>(m) * RR + e];
+    V[e] = v;
+  }
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = V[k * R + k];
+      if (!(d > 0.0)) bad = 1;
+      V[k * R + k] = sqrt(d);
+    }
+    __syncthreads();
+    const double dk = V[k * R + k];
+    for (int i = k + 1 + threadIdx.x; i < R; i += kT) V[i * R + k] /= dk;
+    __syncthreads();
+    for (int e = threadIdx.x; e < RR; e += kT) {
+      const int i = e / R, j = e - i * R;
+      if (i > k && j > k && j <= i) V[e] -= V[i * R + k] * V[j * R + k];
+    }
+    __syncthreads();
+  }
+  // Li = L^{-1}, column j solved by thread j
+  for (int j = threadIdx.x; j < R; j += kT) {
+    for (int i = 0; i < R; ++i) {
+      if (i < j) {
+        Li[i * R + j] = 0.0;
+        continue;
+      }
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = j; k < i; ++k) s -= V[i * R + k] * Li[k * R + j];
+      Li[i * R + j] = s / V[i * R + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RR; e += kT) {
+    const int a = e / R, b = e - a * R;
+    double s = 0.0;
+    for (int k = a > b ? a : b; k < R; ++k) s += Li[k * R + a] * Li[k * R + b];
+    vinv64[e] = s;
+    vinv32[e] = static_cast<float>(s);
+  }
+  if (threadIdx.x == 0 && bad) set_status(status, ALTO_ENOTSPD);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  // non-negative doubles order like their bit patterns
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+// A = Mt V^{-1} row by row; column statistics (sum of squares or max |.|).
+template <typename C>
+__global__ void __launch_bounds__(kT) solve_kernel(const C* __restrict__ Mt, int64_t I, int R,
+                                                   const C* __restrict__ vinv, C* __restrict__ A,
+                                                   double* __restrict__ colstat, int use_max) {
+  __shared__ C sV[kMaxR * kMaxR];
+  __shared__ double red[kT];
+  for (int e = threadIdx.x; e < R * R; e += kT) sV[e] = vinv[e];
+  __syncthreads();
+  const int per = kT / R;  // rows per pass
+  const int rr = threadIdx.x / R, col = threadIdx.x - rr * R;
+  C stat = C(0);
+  if (rr < per) {
+    for (int64_t row = static_cast<int64_t>(blockIdx.x) * per + rr; row < I;
+         row += static_cast<int64_t>(gridDim.x) * per) {
+      const C* m = Mt + row * R;
+      C acc = C(0);
+      for (int k = 0; k < R; ++k) acc += m[k] * sV[k * R + col];
+      A[row * R + col] = acc;
+      if (use_max)
+        stat = fmax(stat, fabs(acc));
+      else
+        stat += acc * acc;
+    }
+  }
+  red[threadIdx.x] = (rr < per) ? static_cast<double>(stat) : 0.0;
+  __syncthreads();
+  if (threadIdx.x < R) {
+    double s = 0.0;
+    for (int q = 0; q < per; ++q) {
+      const double v = red[q * R + threadIdx.x];
+      s = use_max ? fmax(s, v) : s + v;
+    }
+    if (use_max)
+      atomic_max_nonneg(colstat + threadIdx.x, s);
+    else
+      atomicAdd(colstat + threadIdx.x, s);
+  }
+}
+
+// U = A / lambda (stored as FT), G += U^T U, and optionally
+// ip += sum_r lambda_r sum_i U[i,r] Mt[i,r].
+template <typename FT>
+__global__ void __launch_bounds__(kT) normalize_gram_kernel(const typename CT<FT>::type* __restrict__ A,
+                                                            int64_t I, int R,
+                                                            const double* __restrict__ colstat,
+                                                            int use_max, double* __restrict__ lambda,
+                                                            FT* __restrict__ U, double* __restrict__ G,
+                                                            const typename CT<FT>::type* __restrict__ Mt,
+                                                            double* __restrict__ ip) {
+  using C = typename CT<FT>::type;
+  __shared__ C tile[kGramRows][kMaxR];
+  __shared__ C inv[kMaxR];
+  __shared__ double lam[kMaxR];
+  __shared__ double ipred[kT];
+  constexpr int Q = kMaxR * kMaxR / kT;
+  for (int r = threadIdx.x; r < R; r += kT) {
+    const double l = use_max ? fmax(colstat[r], 1.0) : sqrt(colstat[r]);
+    lam[r] = l;
+    inv[r] = static_cast<C>(1.0 / l);
+    if (blockIdx.x == 0) lambda[r] = l;
+  }
+  C part[Q];
+  double acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    part[q] = C(0);
+    acc[q] = 0.0;
+  }
+  double ipd = 0.0;
+  int since = 0;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * kGramRows; r0 < I;
+       r0 += static_cast<int64_t>(gridDim.x) * kGramRows) {
+    const int64_t rows = I - r0 < kGramRows ? I - r0 : kGramRows;
+    __syncthreads();
+    C ipart = C(0);
+    for (int i = threadIdx.x; i < kGramRows * R; i += kT) {
+      const int rr = i / R, cc = i - rr * R;
+      C u = C(0);
+      if (rr < rows) {
+        const int64_t e = (r0 + rr) * R + cc;
+        const FT stored = static_cast<FT>(A[e] * inv[cc]);
+        U[e] = stored;
+        u = to_ct<FT>(stored);
+        if (Mt != nullptr) ipart += u * Mt[e] * static_cast<C>(lam[cc]);
+      }
+      tile[rr][cc] = u;
+    }
+    ipd += static_cast<double>(ipart);
+    __syncthreads();
+    gram_tile<C>(tile, R, part);
+    if (++since == 16) {
+      gram_flush<C>(part, acc, R);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) part[q] = C(0);
+      since = 0;
+    }
+  }
+  gram_flush<C>(part, acc, R);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = threadIdx.x + q * kT;
+    if (e < R * R) atomicAdd(G + e, acc[q]);
+  }
+  if (Mt != nullptr) {
+    ipred[threadIdx.x] = ipd;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) ipred[threadIdx.x] += ipred[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(ip, ipred[0]);
+  }
+}
+
+// fit = 1 - sqrt(max(0, ||X||^2 + lambda^T (Hadamard G) lambda - 2 ip)) / ||X||
+__global__ void __launch_bounds__(kT) fit_kernel(const double* __restrict__ G, int N, int R,
+                                                 const double* __restrict__ lambda, double normX2,
+                                                 const double* __restrict__ ip, double* __restrict__ fit) {
+  __shared__ double red[kT];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < R * R; e += kT) {
+    const int a = e / R, b = e - a * R;
+    double v = lambda[a] * lambda[b];
+    for (int m = 0; m < N; ++m) v *= G[static_cast<size_t>(m) * R * R + e];
+    s += v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double res2 = normX2 + red[0] - 2.0 * ip[0];
+    const double res = sqrt(res2 > 0.0 ? res2 : 0.0);
+    *fit = 1.0 - res / sqrt(normX2);
+  }
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+unsigned rows_grid(int64_t I, int rows_per_block, int per_sm) {
+  int64_t g = (I + rows_per_block - 1) / rows_per_block;
+  const int64_t cap = static_cast<int64_t>(sm_count()) * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<unsigned>(g);
+}
+
+template <typename FT>
+cudaError_t launch_gram(const void* A, int64_t I, int R, double* G, cudaStream_t s) {
+  if (I <= 0) return cudaSuccess;
+  gram_kernel<FT><<<rows_grid(I, kGramRows, 4), kT, 0, s>>>(static_cast<const FT*>(A), I, R, G);
+  note_launch();
+  return cudaGetLastError();
+}
+
+#define CK(expr)                                                                 \
+  do {                                                                           \
+    const cudaError_t e_ = (expr);                                               \
+    if (e_ != cudaSuccess) return fail(ALTO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename FT>
+alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors, double* lambda,
+                        double* fit, cudaStream_t s) {
+  using C = typename CT<FT>::type;
+  const int N = t->lay.N;
+  CpalsWork& w = t->cp;
+  const size_t RR = static_cast<size_t>(R) * R;
+  // initial Gram matrices
+  CK(cudaMemsetAsync(w.gram, 0, sizeof(double) * N * RR, s));
+  for (int m = 0; m < N; ++m)
+    CK(launch_gram<FT>(factors[m], static_cast<int64_t>(t->lay.dims[m]), R, w.gram + m * RR, s));
+  const alto_dtype fd = std::is_same<FT, double>::value ? ALTO_F64
+                        : std::is_same<FT, float>::value ? ALTO_F32
+                                                          : ALTO_BF16;
+  for (int it = 0; it < iters; ++it) {
+    for (int n = 0; n < N; ++n) {
+      const int64_t In = static_cast<int64_t>(t->lay.dims[n]);
+      alto_status st = run_mttkrp(t, n, factors, R, fd, w.mt, ALTO_VAR_AUTO, s);
+      if (st != ALTO_OK) return st;
+      chol_inv_kernel<<<1, kT, 0, s>>>(w.gram, N, n, R, w.vinv64, w.vinv32, t->status);
+      note_launch();
+      CK(cudaGetLastError());
+      CK(cudaMemsetAsync(w.colstat, 0, sizeof(double) * R, s));
+      const int use_max = it > 0 ? 1 : 0;
+      const C* vinv = std::is_same<C, double>::value ? reinterpret_cast<const C*>(w.vinv64)
+                                                      : reinterpret_cast<const C*>(w.vinv32);
+      if (In > 0) {
+        solve_kernel<C><<<rows_grid(In, kT / R, 8), kT, 0, s>>>(static_cast<const C*>(w.mt), In, R, vinv,
+                                                               static_cast<C*>(w.atmp), w.colstat, use_max);
+        note_launch();
+        CK(cudaGetLastError());
+      }
+      CK(cudaMemsetAsync(w.gram + n * RR, 0, sizeof(double) * RR, s));
+      const bool last = (n == N - 1);
+      if (last) CK(cudaMemsetAsync(w.scal, 0, sizeof(double), s));
+      normalize_gram_kernel<FT><<<rows_grid(In, kGramRows, 4), kT, 0, s>>>(
+          static_cast<const C*>(w.atmp), In, R, w.colstat, use_max, lambda, static_cast<FT*>(factors[n]),
+          w.gram + n * RR, last ? static_cast<const C*>(w.mt) : nullptr, w.scal);
+      note_launch();
+      CK(cudaGetLastError());
+    }
+    fit_kernel<<<1, kT, 0, s>>>(w.gram, N, R, lambda, t->normX2, w.scal, w.fits + it);
+    note_launch();
+    CK(cudaGetLastError());
+  }
+  if (fit != nullptr && iters > 0) {
+    CK(cudaMemcpyAsync(fit, w.fits, sizeof(double) * iters, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return ALTO_OK;
+}
+
+}  // namespace
+
+alto_status run_cpals(alto_tensor_s* t, int R, int iters, void* const* factors, alto_dtype fdtype,
+                      double* lambda, double* fit, cudaStream_t s) {
+  const int N = t->lay.N;
+  if (R < 1 || R > kMaxR) return fail(ALTO_EINVAL, "CP-ALS rank %d outside [1, %d]", R, kMaxR);
+  if (iters < 0) return fail(ALTO_EINVAL, "iters must be >= 0");
+  if (factors == nullptr || lambda == nullptr) return fail(ALTO_EINVAL, "null factors or lambda");
+  for (int m = 0; m < N; ++m)
+    if (factors[m] == nullptr) return fail(ALTO_EINVAL, "factor %d is null", m);
+  if (fdtype == ALTO_F64 && t->vdtype != ALTO_F64)
+    return fail(ALTO_EINVAL, "FP64 factors need FP64 values");
+  if (fdtype != ALTO_F64 && t->vdtype != ALTO_F32)
+    return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 values");
+  CpalsWork& w = t->cp;
+  const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
+  uint64_t maxI = 0;
+  for (int m = 0; m < N; ++m) maxI = t->lay.dims[m] > maxI ? t->lay.dims[m] : maxI;
+  if (w.R != R || w.fdtype != fdtype || w.fits_cap < iters || w.mt == nullptr) {
+    dev_free(t, w.mt);
+    dev_free(t, w.atmp);
+    dev_free(t, w.gram);
+    dev_free(t, w.vinv64);
+    dev_free(t, w.vinv32);
+    dev_free(t, w.colstat);
+    dev_free(t, w.scal);
+    dev_free(t, w.fits);
+    std::memset(&w, 0, sizeof(w));
+    const int cap = iters > 16 ? iters : 16;
+    w.mt = dev_alloc(t, maxI * R * osz);
+    w.atmp = dev_alloc(t, maxI * R * osz);
+    w.gram = static_cast<double*>(dev_alloc(t, sizeof(double) * N * R * R));
+    w.vinv64 = static_cast<double*>(dev_alloc(t, sizeof(double) * R * R));
+    w.vinv32 = static_cast<float*>(dev_alloc(t, sizeof(float) * R * R));
+    w.colstat = static_cast<double*>(dev_alloc(t, sizeof(double) * R));
+    w.scal = static_cast<double*>(dev_alloc(t, sizeof(double) * 4));
+    w.fits = static_cast<double*>(dev_alloc(t, sizeof(double) * cap));
+    if (!w.mt || !w.atmp || !w.gram || !w.vinv64 || !w.vinv32 || !w.colstat || !w.scal || !w.fits)
+      return fail(ALTO_ENOMEM, "CP-ALS workspace allocation failed");
+    w.R = R;
+    w.fdtype = fdtype;
+    w.fits_cap = cap;
+  }
+  switch (fdtype) {
+    case ALTO_F64: return cpals_typed<double>(t, R, iters, factors, lambda, fit, s);
+    case ALTO_F32: return cpals_typed<float>(t, R, iters, factors, lambda, fit, s);
+    case ALTO_BF16: return cpals_typed<__nv_bfloat16>(t, R, iters, factors, lambda, fit, s);
+  }
+  return fail(ALTO_EINVAL, "bad factor dtype");
+}
+
+}  // namespace alto

@@ -1,0 +1,330 @@
+// ALTO generation kernels other than the sort (Sec. 3.1-3.3):
+//   encode         linearization: bit-level gather of every mode index into
+//                  one key (Sec. 3.1);
+//   permute        values into ALTO order;
+//   sumsq          ||X||^2 for the CP-ALS fit (duplicates summed first);
+//   segment_stats  per-segment mode intervals T_{l,n} (Sec. 3.2), plus the
+//                  first and last segment touching every row, from which the
+//                  distinct-row counts and the helper flags follow;
+//   set_flags      boundary/internal helper flags in the spare key bits
+//                  (Sec. 3.3).
+#include "internal.h"
+
+namespace alto {
+
+namespace {
+
+struct EncodeParams {
+  int nmodes;
+  uint64_t dims[kMaxModes];
+  int nbits[kMaxModes];
+  uint8_t pos[kMaxModes][32];
+};
+
+template <typename IT, int KW>
+__global__ void __launch_bounds__(256) encode_kernel(const __grid_constant__ EncodeParams ep,
+                                                     const __grid_constant__ IdxPtrs idx, int64_t M,
+                                                     uint64_t* __restrict__ keys, int* status) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride) {
+    uint64_t w[2] = {0, 0};
+    for (int n = 0; n < ep.nmodes; ++n) {
+      uint64_t i = static_cast<uint64_t>(__ldcs(static_cast<const IT*>(idx.p[n]) + x));
+      if (i >= ep.dims[n]) {
+        set_status(status, ALTO_ERANGE);
+        i = 0;
+      }
+      for (int l = 0; l < ep.nbits[n]; ++l) {
+        const int p = ep.pos[n][l];
+        w[p >> 6] |= ((i >> l) & 1ull) << (p & 63);
+      }
+    }
+    keys[x * KW] = w[0];
+    if (KW == 2) keys[x * KW + 1] = w[1];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) permute_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                      const uint32_t* __restrict__ perm, int64_t M) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride)
+    dst[x] = src[perm[x]];
+}
+
+// ||X||^2 where X sums duplicate coordinates: over the ordered keys, every
+// run of equal keys contributes (sum of its values)^2.
+template <typename T, int KW>
+__global__ void __launch_bounds__(256) sumsq_kernel(const uint64_t* __restrict__ keys,
+                                                    const T* __restrict__ v, int64_t M, double* out) {
+  double s = 0.0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride) {
+    bool start = x == 0;
+    if (!start) {
+#pragma unroll
+      for (int w = 0; w < KW; ++w) start |= keys[x * KW + w] != keys[(x - 1) * KW + w];
+    }
+    if (!start) continue;
+    double run = static_cast<double>(v[x]);
+    for (int64_t y = x + 1; y < M; ++y) {
+      bool same = true;
+#pragma unroll
+      for (int w = 0; w < KW; ++w) same &= keys[y * KW + w] == keys[x * KW + w];
+      if (!same) break;
+      run += static_cast<double>(v[y]);
+    }
+    s += run * run;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+struct RowArrays {
+  uint32_t* first[kMaxModes];
+  uint32_t* last[kMaxModes];
+};
+
+// One warp per segment.  Lanes walk the segment, decode every mode, keep
+// running min/max, and record the lowest / highest segment that touches
+// each row (atomicMin / atomicMax; a lane skips the atomic when its
+// previous element had the same row).
+template <int KW>
+__global__ void __launch_bounds__(256) segment_stats_kernel(const __grid_constant__ DecodeParams dp,
+                                                            const uint64_t* __restrict__ keys,
+                                                            int64_t M, int64_t L,
+                                                            uint32_t* __restrict__ ivl,
+                                                            const __grid_constant__ RowArrays ra) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int N = dp.nmodes;
+  for (int64_t seg = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+       seg < L; seg += nwarps) {
+    const int64_t s0 = seg_begin(seg, M, L), s1 = seg_begin(seg + 1, M, L);
+    uint32_t lo[kMaxModes], hi[kMaxModes], prev[kMaxModes];
+#pragma unroll
+    for (int n = 0; n < kMaxModes; ++n) {
+      lo[n] = 0xffffffffu;
+      hi[n] = 0;
+      prev[n] = 0xffffffffu;
+    }
+    for (int64_t x = s0 + lane; x < s1; x += 32) {
+      const KeyT<KW> k = load_key<KW>(keys, x);
+#pragma unroll
+      for (int n = 0; n < kMaxModes; ++n) {
+        if (n < N) {
+          const uint32_t i = extract<KW>(k, dp, n);
+          lo[n] = min(lo[n], i);
+          hi[n] = max(hi[n], i);
+          if (i != prev[n]) {
+            atomicMin(ra.first[n] + i, static_cast<uint32_t>(seg));
+            if (ra.last[n] != nullptr) atomicMax(ra.last[n] + i, static_cast<uint32_t>(seg));
+            prev[n] = i;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < kMaxModes; ++n) {
+      if (n < N) {
+        uint32_t a = lo[n], b = hi[n];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+          b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) {
+          if (s1 <= s0) {  // empty segment: (1, 0)
+            a = 1;
+            b = 0;
+          }
+          ivl[(seg * N + n) * 2 + 0] = a;
+          ivl[(seg * N + n) * 2 + 1] = b;
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) count_touched_kernel(const uint32_t* __restrict__ first,
+                                                            uint64_t n, unsigned long long* out) {
+  unsigned long long c = 0;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t r = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride)
+    c += first[r] != 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void __launch_bounds__(256) max_interval_kernel(const uint32_t* __restrict__ ivl, int64_t L,
+                                                           int N, unsigned long long* out) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < L * N; j += stride) {
+    const uint32_t a = ivl[2 * j], b = ivl[2 * j + 1];
+    if (b >= a) atomicMax(out + (j % N), static_cast<unsigned long long>(b - a) + 1ull);
+  }
+}
+
+struct FlagParams {
+  int nflag;
+  int slot[kMaxModes];  // decode slot (= mode) of each flagged mode
+  int bit[kMaxModes];   // key bit of its flag
+};
+
+template <int KW>
+__global__ void __launch_bounds__(256) set_flags_kernel(const __grid_constant__ DecodeParams dp,
+                                                        const __grid_constant__ FlagParams fp,
+                                                        uint64_t* __restrict__ keys, int64_t M,
+                                                        const __grid_constant__ RowArrays ra) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride) {
+    const KeyT<KW> k = load_key<KW>(keys, x);
+    uint64_t w[2] = {0, 0};
+    for (int f = 0; f < fp.nflag; ++f) {
+      const int n = fp.slot[f];
+      const uint32_t i = extract<KW>(k, dp, n);
+      if (ra.first[n][i] == ra.last[n][i]) w[fp.bit[f] >> 6] |= 1ull << (fp.bit[f] & 63);
+    }
+    keys[x * KW] |= w[0];
+    if (KW == 2) keys[x * KW + 1] |= w[1];
+  }
+}
+
+unsigned grid_for(int64_t work, int per_block) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return static_cast<unsigned>(g);
+}
+
+}  // namespace
+
+cudaError_t launch_encode(const Layout& lay, const IdxPtrs& idx, int idx_bytes, int64_t M,
+                          uint64_t* keys, int* status, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  EncodeParams ep{};
+  ep.nmodes = lay.N;
+  for (int n = 0; n < lay.N; ++n) {
+    ep.dims[n] = lay.dims[n];
+    ep.nbits[n] = lay.nbits[n];
+    for (int l = 0; l < lay.nbits[n]; ++l) ep.pos[n][l] = static_cast<uint8_t>(lay.pos[n][l]);
+  }
+  const unsigned g = grid_for(M, 256);
+  if (idx_bytes == 4) {
+    if (lay.KW == 1)
+      encode_kernel<uint32_t, 1><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+    else
+      encode_kernel<uint32_t, 2><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+  } else {
+    if (lay.KW == 1)
+      encode_kernel<int64_t, 1><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+    else
+      encode_kernel<int64_t, 2><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const void* src, void* dst, const uint32_t* perm, int64_t M,
+                           int elem_bytes, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  const unsigned g = grid_for(M, 256);
+  if (elem_bytes == 8)
+    permute_kernel<uint64_t><<<g, 256, 0, s>>>(static_cast<const uint64_t*>(src),
+                                               static_cast<uint64_t*>(dst), perm, M);
+  else
+    permute_kernel<uint32_t><<<g, 256, 0, s>>>(static_cast<const uint32_t*>(src),
+                                               static_cast<uint32_t*>(dst), perm, M);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dtype vd, int64_t M,
+                         double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess || M <= 0) return e;
+  const unsigned g = grid_for(M, 256 * 8);
+  if (vd == ALTO_F64) {
+    if (KW == 1)
+      sumsq_kernel<double, 1><<<g, 256, 0, s>>>(keys, static_cast<const double*>(vals), M, out);
+    else
+      sumsq_kernel<double, 2><<<g, 256, 0, s>>>(keys, static_cast<const double*>(vals), M, out);
+  } else {
+    if (KW == 1)
+      sumsq_kernel<float, 1><<<g, 256, 0, s>>>(keys, static_cast<const float*>(vals), M, out);
+    else
+      sumsq_kernel<float, 2><<<g, 256, 0, s>>>(keys, static_cast<const float*>(vals), M, out);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_stats(const Layout& lay, const uint64_t* keys, int64_t M, int64_t L,
+                                 uint32_t* ivl, uint32_t* const* first, uint32_t* const* last,
+                                 cudaStream_t s) {
+  if (L <= 0) return cudaSuccess;
+  DecodeParams dp;
+  int ident[kMaxModes];
+  for (int n = 0; n < kMaxModes; ++n) ident[n] = n;
+  make_decode(lay, ident, &dp);
+  RowArrays ra{};
+  for (int n = 0; n < lay.N; ++n) {
+    ra.first[n] = first[n];
+    ra.last[n] = last[n];
+  }
+  const unsigned g = grid_for(L, 8);
+  if (lay.KW == 1)
+    segment_stats_kernel<1><<<g, 256, 0, s>>>(dp, keys, M, L, ivl, ra);
+  else
+    segment_stats_kernel<2><<<g, 256, 0, s>>>(dp, keys, M, L, ivl, ra);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_touched(const uint32_t* first, uint64_t n, unsigned long long* out,
+                                 cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  count_touched_kernel<<<grid_for(static_cast<int64_t>(n), 256 * 8), 256, 0, s>>>(first, n, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_interval(const uint32_t* ivl, int64_t L, int N, unsigned long long* out,
+                                cudaStream_t s) {
+  if (L <= 0) return cudaSuccess;
+  max_interval_kernel<<<grid_for(L * N, 256), 256, 0, s>>>(ivl, L, N, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_flags(const Layout& lay, uint64_t* keys, int64_t M,
+                             uint32_t* const* first, uint32_t* const* last, cudaStream_t s) {
+  FlagParams fp{};
+  for (int n = 0; n < lay.N; ++n)
+    if (lay.flag_bit[n] >= 0) {
+      fp.slot[fp.nflag] = n;
+      fp.bit[fp.nflag] = lay.flag_bit[n];
+      fp.nflag++;
+    }
+  if (fp.nflag == 0 || M <= 0) return cudaSuccess;
+  DecodeParams dp;
+  int ident[kMaxModes];
+  for (int n = 0; n < kMaxModes; ++n) ident[n] = n;
+  make_decode(lay, ident, &dp);
+  RowArrays ra{};
+  for (int n = 0; n < lay.N; ++n) {
+    ra.first[n] = first[n];
+    ra.last[n] = last[n];
+  }
+  const unsigned g = grid_for(M, 256);
+  if (lay.KW == 1)
+    set_flags_kernel<1><<<g, 256, 0, s>>>(dp, fp, keys, M, ra);
+  else
+    set_flags_kernel<2><<<g, 256, 0, s>>>(dp, fp, keys, M, ra);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace alto

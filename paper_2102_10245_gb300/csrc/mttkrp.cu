@@ -1,0 +1,119 @@
+// Host side of alto_mttkrp: argument checks, slot order, variant choice and
+// dispatch to the per-dtype kernel instantiations.
+#include <algorithm>
+
+#include "mttkrp_kernels.cuh"
+
+namespace alto {
+
+namespace {
+
+constexpr size_t kSmemTempBytes = 96 * 1024;  // shared Temp budget per block
+
+int device_sms() {
+  static int cached[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = s > 0 ? s : 1;
+  }
+  return cached[dev];
+}
+
+int smem_rows_for(const alto_tensor_s* t, int mode, int R, size_t osz) {
+  size_t rows = kSmemTempBytes / (static_cast<size_t>(R) * osz);
+  if (rows > t->lay.dims[mode]) rows = static_cast<size_t>(t->lay.dims[mode]);
+  return static_cast<int>(rows);
+}
+
+}  // namespace
+
+cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors, int R,
+                          alto_dtype fdtype, void* out, int variant, size_t osz, cudaStream_t s);
+
+// The Sec. 3.3 rule adapted to the GPU: fiber reuse M / I_n above 4 means
+// buffered accumulation; the buffer is shared memory when nine in ten
+// blocks' output intervals fit there, otherwise warp-level aggregation in
+// registers.  Reuse of at most 4 means direct atomics.
+int auto_variant(const alto_tensor_s* t, int mode, int R, size_t osz) {
+  if (t->reuse[mode] <= 4.0) return ALTO_VAR_ATOMIC;
+  const int rows = smem_rows_for(t, mode, R, osz);
+  if (t->unit_fit_frac(mode, static_cast<uint64_t>(rows)) >= 0.9) return ALTO_VAR_SMEM;
+  return ALTO_VAR_WARPAGG;
+}
+
+alto_status run_mttkrp(alto_tensor_s* t, int mode, const void* const* factors, int R,
+                       alto_dtype fdtype, void* out, int variant, cudaStream_t s) {
+  const Layout& lay = t->lay;
+  const int N = lay.N;
+  if (mode < 0 || mode >= N) return fail(ALTO_EINVAL, "mode %d outside [0, %d)", mode, N);
+  if (R < 1) return fail(ALTO_EINVAL, "rank %d < 1", R);
+  if (out == nullptr || factors == nullptr) return fail(ALTO_EINVAL, "null factors or output");
+  for (int m = 0; m < N; ++m)
+    if (m != mode && factors[m] == nullptr) return fail(ALTO_EINVAL, "factor %d is null", m);
+  if (fdtype == ALTO_F64) {
+    if (t->vdtype != ALTO_F64) return fail(ALTO_EINVAL, "FP64 factors need FP64 values");
+  } else if (fdtype == ALTO_F32 || fdtype == ALTO_BF16) {
+    if (t->vdtype != ALTO_F32) return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 values");
+  } else {
+    return fail(ALTO_EINVAL, "bad factor dtype %d", static_cast<int>(fdtype));
+  }
+  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
+  cudaError_t e = prof_begin(t, mode, s);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "profiling event: %s", cudaGetErrorString(e));
+  e = mttkrp_launch(t, mode, factors, R, fdtype, out, variant, osz, s);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "MTTKRP launch: %s", cudaGetErrorString(e));
+  e = prof_end(t, s);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "profiling event: %s", cudaGetErrorString(e));
+  return ALTO_OK;
+}
+
+cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors, int R,
+                          alto_dtype fdtype, void* out, int variant, size_t osz, cudaStream_t s) {
+  const Layout& lay = t->lay;
+  const int N = lay.N;
+  cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(lay.dims[mode]) * R * osz, s);
+  if (e != cudaSuccess) return e;
+  if (t->M == 0) return cudaSuccess;
+
+  int v = variant != ALTO_VAR_AUTO ? variant : t->variant[mode];
+  if (v == ALTO_VAR_AUTO) v = auto_variant(t, mode, R, osz);
+
+  MttkrpLaunch l{};
+  int slot_mode[kMaxModes];
+  int k = 0;
+  for (int m = 0; m < N; ++m)
+    if (m != mode) slot_mode[k++] = m;
+  slot_mode[k] = mode;
+  make_decode(lay, slot_mode, &l.args.dp);
+  l.args.keys = t->keys;
+  l.args.vals = t->vals;
+  l.args.M = t->M;
+  l.args.L = t->L;
+  for (int sl = 0; sl < N; ++sl) l.args.f[sl] = factors[slot_mode[sl]];
+  l.args.out = out;
+  l.args.R = R;
+  l.args.out_mode = mode;
+  l.args.ivl = t->ivl;
+  l.N = N;
+  l.KW = lay.KW;
+  l.sms = device_sms();
+  if (v == ALTO_VAR_TEMP) return launch_temp_variant(t, l, fdtype, osz, s);
+  l.variant = v;
+  if (v == ALTO_VAR_SMEM) {
+    const int rows = smem_rows_for(t, mode, R, osz);
+    l.args.smem_rows = rows;
+    l.smem_dyn = static_cast<size_t>(rows) * R * osz + static_cast<size_t>((rows + 31) / 32) * 4;
+  }
+  switch (fdtype) {
+    case ALTO_F64: return mttkrp_dispatch_f64(l, s);
+    case ALTO_F32: return mttkrp_dispatch_f32(l, s);
+    default: return mttkrp_dispatch_bf16(l, s);
+  }
+}
+
+}  // namespace alto

@@ -1,0 +1,96 @@
+"""CP-ALS over ALTO MTTKRP on the GPU against the oracle's Kolda-Bader
+CP-ALS (Sec. 2.2): per-iteration fit, lambda and factors."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import dev, make, rel_err, to_bf16_exact
+
+pytestmark = pytest.mark.gpu
+
+
+def test_small_uniform_fp64_matches_oracle():
+    cfg = synth.CONFIGS["uniform3d-64x128x256"]
+    dims, idx, vals = synth.tensor(cfg)
+    U0 = synth.factors(cfg)
+    at = make(dims, idx, vals)
+    Ud = [dev(u.copy()) for u in U0]
+    lam, fits = at.cpals(Ud, cfg["iters"])
+    U, lam_o, fits_o, _ = oracle.cpals(dims, idx, vals, U0, cfg["iters"])
+    print("fits gpu", fits, "oracle", fits_o)
+    assert np.allclose(fits, fits_o, rtol=0, atol=1e-10)
+    assert rel_err(lam.cpu().numpy(), lam_o) <= 1e-9
+    for n in range(3):
+        e = rel_err(Ud[n].cpu().numpy(), U[n])
+        print("factor %d rel err %.3e" % (n, e))
+        assert e <= 1e-9
+
+
+@pytest.mark.parametrize("name,nnz", [("zipf3d-4Mx4Mx30k", 200_000), ("long5d-2^20x3-2^16x2", 200_000)])
+def test_scaled_fp32_matches_oracle(name, nnz):
+    cfg = synth.scaled(name, nnz=nnz, dims=None)
+    # shrink the mode lengths so the oracle's dense Gram work stays small
+    cfg["dims"] = tuple(min(d, 20_000) for d in cfg["dims"])
+    dims, idx, vals = synth.tensor(cfg)
+    U0 = synth.factors(cfg)
+    at = make(dims, idx, vals)
+    Ud = [dev(u.copy()) for u in U0]
+    iters = 3
+    lam, fits = at.cpals(Ud, iters)
+    U, lam_o, fits_o, _ = oracle.cpals(dims, idx, vals, [u.astype(np.float64) for u in U0], iters)
+    print(name, "fits gpu", fits, "oracle", fits_o)
+    assert np.allclose(fits, fits_o, rtol=0, atol=1e-4)
+    for n in range(len(dims)):
+        e = rel_err(Ud[n].cpu().numpy(), U[n])
+        print("factor %d rel err %.3e" % (n, e))
+        assert e <= 1e-2
+
+
+def test_bf16_factors_track_fp32():
+    cfg = synth.scaled("zipf3d-4Mx4Mx30k", nnz=200_000)
+    cfg["dims"] = (20_000, 20_000, 3000)
+    dims, idx, vals = synth.tensor(cfg)
+    U0 = synth.factors(cfg)
+    at = make(dims, idx, vals)
+    Uf = [dev(u.copy()) for u in U0]
+    _, fits32 = at.cpals(Uf, 3)
+    Ub = [to_bf16_exact(u)[0] for u in U0]
+    _, fitsb = at.cpals(Ub, 3)
+    print("fp32", fits32, "bf16", fitsb)
+    assert all(abs(a - b) < 2e-2 for a, b in zip(fits32, fitsb))
+
+
+def test_exact_recovery_dense_low_rank():
+    rng = np.random.default_rng(1)
+    dims = (9, 8, 7)
+    R = 3
+    T = [rng.standard_normal((d, R)) for d in dims]
+    X = np.einsum("ir,jr,kr->ijk", *T)
+    cells = np.array(list(itertools.product(*[range(d) for d in dims])))
+    idx = [cells[:, n].astype(np.uint32) for n in range(3)]
+    vals = X[tuple(cells.T)]
+    at = make(dims, idx, vals)
+    Ud = [dev(t + 0.05 * rng.standard_normal(t.shape)) for t in T]
+    lam, fits = at.cpals(Ud, 40)
+    print("final fit", fits[-1])
+    assert fits[-1] > 1 - 1e-6
+    assert all(b >= a - 1e-9 for a, b in zip(fits, fits[1:]))
+
+
+def test_singular_gram_reports_not_spd():
+    from paper_2102_10245_gb300 import AltoError
+    cfg = synth.CONFIGS["uniform3d-64x128x256"]
+    dims, idx, vals = synth.tensor(cfg)
+    U0 = synth.factors(cfg)
+    U0[1][:, 3] = 0.0                 # zero column: V is singular
+    at = make(dims, idx, vals)
+    with pytest.raises(AltoError) as e:
+        at.cpals([dev(u.copy()) for u in U0], 1)
+    assert e.value.status == 6        # ALTO_ENOTSPD
+    # the handle and the context stay usable
+    lam, fits = at.cpals([dev(u.copy()) for u in synth.factors(cfg)], 1)
+    assert np.isfinite(fits[0])
