@@ -240,6 +240,34 @@ alto_status alto_profile_read(alto_t t, double *ms, int64_t *calls);
  * process so far (all handles). */
 alto_status alto_launch_count(uint64_t *count);
 
+/*
+ * alto_linearize_noalloc -- the linearization and ordering stages of
+ * alto_create (bit-level encode, stable sort) written into caller buffers,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * that runs while a stream is being captured into a CUDA graph, services that
+ * reserve all device memory for their own pool, and embedders whose device
+ * allocator belongs to another runtime.
+ *
+ *   idx   : host array of N DEVICE pointers to nnz indices (idx_bytes 4 or 8).
+ *   keys  : device, nnz x key_words uint64 (key_words from
+ *           alto_layout_for_dims; lo word first), ALTO order, no helper flags.
+ *   perm  : device, nnz uint32, input position of every nonzero in ALTO order.
+ * The sort's scratch lives in one fixed device array of about 5.3 MB that
+ * every GPU which loads libalto holds until the process exits; nnz above
+ * ALTO_NOALLOC_MAX_NNZ is rejected with ALTO_EINVAL.  The first call on each
+ * device looks up that array's device address, so make it before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other host threads on the same device) race and must be
+ * serialised by the caller.  Synchronises `stream` at its end; returns
+ * ALTO_ERANGE when an index is out of range.
+ */
+#define ALTO_NOALLOC_MAX_NNZ 262144
+alto_status alto_linearize_noalloc(int nmodes, const uint64_t *dims,
+                                   int64_t nnz, const void *const *idx,
+                                   int idx_bytes, uint64_t *keys,
+                                   uint32_t *perm, void *stream);
+
 /* alto_destroy -- free everything the handle owns.  NULL is accepted. */
 alto_status alto_destroy(alto_t t);
 

@@ -65,6 +65,7 @@ def lib():
             "alto_profile": [P, I],
             "alto_profile_read": [P, P, P],
             "alto_launch_count": [P],
+            "alto_linearize_noalloc": [I, P, I64, P, I, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)

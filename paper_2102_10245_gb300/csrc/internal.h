@@ -124,6 +124,10 @@ void dev_free(alto_tensor_s* t, void* p);
 alto_status fail(alto_status code, const char* fmt, ...);
 
 // sort.cu
+// 32-bit words of sort scratch (tile counts, offsets, scan partials) for M keys
+constexpr int64_t sort_scratch_words_for(int64_t M) {
+  return 2 * (((M + 4095) / 4096) * 256) + ((((M + 4095) / 4096) * 256 + 8191) / 8192) + 64;
+}
 int64_t sort_scratch_words(int64_t M);
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
                                cudaStream_t s);

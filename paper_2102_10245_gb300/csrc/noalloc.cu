@@ -1,0 +1,108 @@
+// alto_linearize_noalloc: ALTO linearization and ordering into caller
+// buffers, with every scratch buffer in one fixed, file-scope device array,
+// so the call never allocates device memory.
+//
+// Some callers cannot allocate: code that runs while a stream is being
+// captured into a CUDA graph (cudaMalloc is not allowed there), services that
+// pre-reserve all device memory for their own pool, and embedders whose
+// allocator is owned by another runtime.  They still pass their own inputs and
+// outputs; this entry point supplies the sort's scratch itself.
+//
+// The array is kNoAllocBytes of device memory that every GPU which loads
+// libalto keeps until the process exits.  All calls share it: two calls whose
+// work overlaps on the GPU (different streams, or different host threads on
+// one device) race on it and must be serialised by the caller.
+#include <mutex>
+
+#include "internal.h"
+
+namespace alto {
+
+namespace {
+
+constexpr int64_t kNoAllocMaxNnz = ALTO_NOALLOC_MAX_NNZ;
+// scratch layout, in 8-byte words: alternate keys (2 words per nonzero),
+// alternate positions (uint32), sort counts / offsets / scan partials
+// (uint32), and the status word
+constexpr size_t kKeyAltWords = 2 * static_cast<size_t>(kNoAllocMaxNnz);
+constexpr size_t kPermAltWords = static_cast<size_t>(kNoAllocMaxNnz) / 2;
+constexpr size_t kSortWords = (static_cast<size_t>(sort_scratch_words_for(kNoAllocMaxNnz)) + 1) / 2;
+constexpr size_t kStatusWords = 4;
+constexpr size_t kScratchWords = kKeyAltWords + kPermAltWords + kSortWords + kStatusWords;
+
+__device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
+
+std::mutex g_setup_mutex;
+void* g_scratch_addr[64] = {};
+
+// Device address of the scratch array for the current device.  The array's
+// name in host code only stands in for the symbol; the address the kernels
+// need is looked up once per device.
+alto_status scratch_for_current_device(unsigned long long** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return fail(ALTO_EINVAL, "device ordinal %d not supported", dev);
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(ALTO_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_scratch_addr[dev] = p;
+  }
+  *out = static_cast<unsigned long long*>(g_scratch_addr[dev]);
+  return ALTO_OK;
+}
+
+}  // namespace
+
+}  // namespace alto
+
+using namespace alto;
+
+extern "C" alto_status alto_linearize_noalloc(int nmodes, const uint64_t* dims, int64_t nnz,
+                                              const void* const* idx, int idx_bytes, uint64_t* keys,
+                                              uint32_t* perm, void* stream) {
+  if (dims == nullptr) return fail(ALTO_EINVAL, "null dims");
+  if (nnz < 0 || nnz > kNoAllocMaxNnz)
+    return fail(ALTO_EINVAL, "nnz %lld outside [0, %lld] (the fixed scratch limit)", (long long)nnz,
+                (long long)kNoAllocMaxNnz);
+  if (idx_bytes != 4 && idx_bytes != 8) return fail(ALTO_EINVAL, "idx_bytes must be 4 or 8");
+  Layout lay;
+  alto_status st = make_layout(nmodes, dims, 0, &lay);
+  if (st != ALTO_OK) return st;
+  if (nnz == 0) return ALTO_OK;
+  if (idx == nullptr || keys == nullptr || perm == nullptr) return fail(ALTO_EINVAL, "null buffer");
+  IdxPtrs ip{};
+  for (int n = 0; n < nmodes; ++n) {
+    if (idx[n] == nullptr) return fail(ALTO_EINVAL, "index array %d is null", n);
+    ip.p[n] = idx[n];
+  }
+  unsigned long long* base = nullptr;
+  st = scratch_for_current_device(&base);
+  if (st != ALTO_OK) return st;
+  uint64_t* key_alt = reinterpret_cast<uint64_t*>(base);
+  uint32_t* perm_alt = reinterpret_cast<uint32_t*>(base + kKeyAltWords);
+  uint32_t* sort_scratch = reinterpret_cast<uint32_t*>(base + kKeyAltWords + kPermAltWords);
+  int* status = reinterpret_cast<int*>(base + kKeyAltWords + kPermAltWords + kSortWords);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // The sort ping-pongs between two buffers; start in the scratch one when the
+  // pass count is odd so that the result lands in the caller's buffers.
+  const int passes = lay.B > 0 ? (lay.B + 7) / 8 : 1;
+  uint64_t* k0 = (passes & 1) ? key_alt : keys;
+  uint64_t* k1 = (passes & 1) ? keys : key_alt;
+  uint32_t* p0 = (passes & 1) ? perm_alt : perm;
+  uint32_t* p1 = (passes & 1) ? perm : perm_alt;
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_encode(lay, ip, idx_bytes, nnz, k0, status, s);
+  if (e == cudaSuccess) e = radix_sort_pairs(&k0, &k1, &p0, &p1, nnz, lay.KW, lay.B, sort_scratch, s);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "linearize: %s", cudaGetErrorString(e));
+  if (k0 != keys || p0 != perm) return fail(ALTO_ECUDA, "linearize: result not in the caller's buffers");
+  int h = 0;
+  e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "linearize: %s", cudaGetErrorString(e));
+  if (h != 0) return fail(static_cast<alto_status>(h), "an input index is >= its mode length");
+  return ALTO_OK;
+}

@@ -214,12 +214,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply(const uint32_t* __res
 
 }  // namespace
 
-int64_t sort_scratch_words(int64_t M) {
-  const int64_t ntiles = (M + kTile - 1) / kTile;
-  const int64_t ncount = ntiles * kRadix;
-  const int64_t nparts = (ncount + kScanChunk - 1) / kScanChunk;
-  return 2 * ncount + nparts + 64;
-}
+static_assert(kTile == 4096 && kRadix == 256 && kScanChunk == 8192, "sort_scratch_words_for layout");
+
+int64_t sort_scratch_words(int64_t M) { return sort_scratch_words_for(M); }
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* part,
                                cudaStream_t s) {
