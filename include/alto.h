@@ -162,10 +162,27 @@ alto_status alto_cpals(alto_t t, int rank, int iters, void *const *factors,
  *   bits_per_mode : N entries, ceil(log2 I_n).
  *   masks         : N x 2 words (lo, hi): key bits that hold mode n.
  *   key_words     : 1 (64-bit keys) or 2 (128-bit keys).
- *   flag_bit      : N entries, the key bit of mode n's helper flag or -1.
+ *   flag_bit      : N entries, the key bit of mode n's boundary/internal
+ *                   helper flag (Sec. 3.3, modes with reuse <= 4) or -1.
+ *   hot_bit       : N entries, the key bit flagging elements whose mode-n row
+ *                   is one of the mode's hot rows (modes with reuse > 4), or
+ *                   -1.  Both kinds of flag live in the unused key bits above
+ *                   the index and never widen the key.
  */
 alto_status alto_get_layout(alto_t t, int *nmodes, int *bits_per_mode,
-                            uint64_t *masks, int *key_words, int *flag_bit);
+                            uint64_t *masks, int *key_words, int *flag_bit,
+                            int *hot_bit);
+
+/*
+ * alto_get_hot_rows -- the hot rows of one mode, hottest first: the rows
+ * with the largest counts when every 16th nonzero in ALTO order is counted,
+ * at most 1024 of them (all rows whose sampled count reaches the smallest
+ * power of two that keeps the list within that bound, counting only rows
+ * sampled at least twice).  MTTKRP keeps the leading ones in a per-block
+ * shared-memory copy.  rows: host array of at least 1024 entries, or NULL;
+ * count: number of hot rows.
+ */
+alto_status alto_get_hot_rows(alto_t t, int mode, uint32_t *rows, int *count);
 
 /*
  * alto_get_stats -- plan statistics (Sec. 3.2-3.3).  Any output may be NULL.

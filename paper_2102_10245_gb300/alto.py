@@ -54,7 +54,8 @@ def lib():
             "alto_create": [P, I, P, I64, P, I, P, I, P, P],
             "alto_mttkrp": [P, I, P, I, I, P, P],
             "alto_cpals": [P, I, I, P, I, P, P, P],
-            "alto_get_layout": [P, P, P, P, P, P],
+            "alto_get_layout": [P, P, P, P, P, P, P],
+            "alto_get_hot_rows": [P, I, P, P],
             "alto_get_stats": [P, P, P, P, P, P, P],
             "alto_export": [P, P, P, P, P, P],
             "alto_set_variant": [P, I, I],
@@ -205,9 +206,18 @@ class AltoTensor:
         masks = (ctypes.c_uint64 * (2 * N))()
         kw = ctypes.c_int()
         fb = (ctypes.c_int * N)()
-        _check(lib().alto_get_layout(self._h, ctypes.byref(nm), bits, masks, ctypes.byref(kw), fb))
+        hb = (ctypes.c_int * N)()
+        _check(lib().alto_get_layout(self._h, ctypes.byref(nm), bits, masks, ctypes.byref(kw), fb, hb))
         return dict(bits=list(bits), masks=[(masks[2 * n], masks[2 * n + 1]) for n in range(N)],
-                    key_words=kw.value, flag_bit=list(fb))
+                    key_words=kw.value, flag_bit=list(fb), hot_bit=list(hb))
+
+    def hot_rows(self, mode):
+        """The mode's hot rows, hottest first (uint32 numpy array)."""
+        import numpy as np
+        rows = np.zeros(1024, dtype=np.uint32)
+        n = ctypes.c_int()
+        _check(lib().alto_get_hot_rows(self._h, mode, rows.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+        return rows[:n.value].copy()
 
     def stats(self):
         N = self.N

@@ -111,6 +111,14 @@ void free_format(alto_tensor_s* t) {
   dev_free(t, t->vals);
   dev_free(t, t->ivl);
   dev_free(t, t->status);
+  for (int n = 0; n < kMaxModes; ++n) {
+    dev_free(t, t->hot[n]);
+    t->hot[n] = nullptr;
+    t->hot_n[n] = 0;
+  }
+  dev_free(t, t->hot_rep);
+  t->hot_rep = nullptr;
+  t->hot_rep_bytes = 0;
   t->keys = nullptr;
   t->perm = nullptr;
   t->vals = nullptr;
@@ -219,6 +227,10 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
   uint32_t* scratch = nullptr;
   uint32_t* first[kMaxModes] = {};
   uint32_t* last[kMaxModes] = {};
+  uint32_t* cnt[kMaxModes] = {};
+  uint32_t* hotbuf = nullptr;   // 2 * kHotCap (count, row) pairs + counter
+  uint32_t* hotmap[kMaxModes] = {};
+  unsigned long long* hist = nullptr;
   unsigned long long* dstat = nullptr;  // [0..N) distinct, [N..2N) max interval
   double* dnorm = nullptr;
   const void* dvals = vals;
@@ -243,6 +255,16 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     } else {
       nflag = 0;
     }
+  }
+  // hot-row flags for the buffered (reuse > 4) modes, in the bits left over
+  int nhotbit = 0;
+  if (o.use_flags) {
+    int b = lay.B + nflag;
+    for (int n = 0; n < N; ++n)
+      if (t->reuse[n] > 4.0 && b < 64 * KW && lay.dims[n] <= (1ull << 31)) {
+        lay.hot_bit[n] = b++;
+        ++nhotbit;
+      }
   }
   t->lay = lay;
   t->L = nnz > 0 ? (o.nparts > 0 ? (o.nparts < nnz ? o.nparts : nnz) : (nnz + kSegNnz - 1) / kSegNnz) : 1;
@@ -297,15 +319,59 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     for (int n = 0; n < N; ++n) {
       ALLOC(first[n], uint32_t*, sizeof(uint32_t) * lay.dims[n]);
       CK(cudaMemsetAsync(first[n], 0xff, sizeof(uint32_t) * lay.dims[n], s));
+      ALLOC(cnt[n], uint32_t*, sizeof(uint32_t) * lay.dims[n]);
+      CK(cudaMemsetAsync(cnt[n], 0, sizeof(uint32_t) * lay.dims[n], s));
       if (lay.flag_bit[n] >= 0) {
         ALLOC(last[n], uint32_t*, sizeof(uint32_t) * lay.dims[n]);
         CK(cudaMemsetAsync(last[n], 0, sizeof(uint32_t) * lay.dims[n], s));
       }
     }
-    CK(launch_segment_stats(lay, t->keys, nnz, t->L, t->ivl, first, last, s));
+    CK(launch_segment_stats(lay, t->keys, nnz, t->L, t->ivl, first, last, cnt, s));
+    // hot rows per mode: threshold on the sampled counts, hottest first
+    ALLOC(hist, unsigned long long*, sizeof(unsigned long long) * 33);
+    ALLOC(hotbuf, uint32_t*, sizeof(uint32_t) * (2 * kHotCap + 1));
+    for (int n = 0; n < N; ++n) {
+      unsigned long long hh[33] = {};
+      CK(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 33, s));
+      CK(launch_hot_hist(cnt[n], lay.dims[n], hist, s));
+      CK(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int b = 1;
+      unsigned long long above = 0;
+      for (int k = 1; k < 33; ++k) above += hh[k];
+      while (b < 33 && above > static_cast<unsigned long long>(kHotCap)) above -= hh[b++];
+      if (b >= 33 || above == 0) continue;
+      CK(cudaMemsetAsync(hotbuf + 2 * kHotCap, 0, sizeof(uint32_t), s));
+      CK(launch_hot_collect(cnt[n], lay.dims[n], 1u << b, kHotCap, hotbuf, hotbuf + 2 * kHotCap, s));
+      std::vector<uint32_t> h(2 * kHotCap + 1);
+      CK(cudaMemcpyAsync(h.data(), hotbuf, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int nh = static_cast<int>(h[2 * kHotCap] < static_cast<uint32_t>(kHotCap) ? h[2 * kHotCap] : kHotCap);
+      std::vector<std::pair<uint32_t, uint32_t>> pr(nh);
+      for (int k = 0; k < nh; ++k) pr[k] = {h[2 * k], h[2 * k + 1]};
+      std::sort(pr.begin(), pr.end(), [](const std::pair<uint32_t, uint32_t>& x,
+                                         const std::pair<uint32_t, uint32_t>& y) {
+        return x.first != y.first ? x.first > y.first : x.second < y.second;
+      });
+      std::vector<uint32_t> rows;
+      for (int k = 0; k < nh; ++k)
+        if (pr[k].second != 0xffffffffu) rows.push_back(pr[k].second);  // that value marks empty slots
+      nh = static_cast<int>(rows.size());
+      ALLOC(t->hot[n], uint32_t*, sizeof(uint32_t) * (nh > 0 ? nh : 1));
+      CK(cudaMemcpyAsync(t->hot[n], rows.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+      t->hot_n[n] = nh;
+      if (lay.hot_bit[n] >= 0 && nh > 0) {
+        const size_t words = (lay.dims[n] + 31) / 32;
+        ALLOC(hotmap[n], uint32_t*, sizeof(uint32_t) * words);
+        CK(cudaMemsetAsync(hotmap[n], 0, sizeof(uint32_t) * words, s));
+        CK(launch_hot_map(t->hot[n], nh, hotmap[n], s));
+      }
+    }
     for (int n = 0; n < N; ++n) CK(launch_count_touched(first[n], lay.dims[n], dstat + n, s));
     CK(launch_max_interval(t->ivl, t->L, N, dstat + kMaxModes, s));
-    if (nflag > 0) CK(launch_set_flags(lay, t->keys, nnz, first, last, s));
+    if (nflag > 0) CK(launch_set_flags(lay, t->keys, nnz, first, last, nullptr, s));
+    if (nhotbit > 0) CK(launch_set_flags(lay, t->keys, nnz, first, last, hotmap, s));
   } else {
     // empty tensor: one empty segment
     std::vector<uint32_t> e(2 * N);
@@ -342,7 +408,11 @@ done:
   for (int n = 0; n < kMaxModes; ++n) {
     dev_free(t, first[n]);
     dev_free(t, last[n]);
+    dev_free(t, cnt[n]);
+    dev_free(t, hotmap[n]);
   }
+  dev_free(t, hotbuf);
+  dev_free(t, hist);
   dev_free(t, dstat);
   dev_free(t, dnorm);
   if (st != ALTO_OK) {
@@ -371,7 +441,7 @@ alto_status alto_cpals(alto_t t, int rank, int iters, void* const* factors, alto
 }
 
 alto_status alto_get_layout(alto_t t, int* nmodes, int* bits_per_mode, uint64_t* masks, int* key_words,
-                            int* flag_bit) {
+                            int* flag_bit, int* hot_bit) {
   if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
   const Layout& L = t->lay;
   if (nmodes) *nmodes = L.N;
@@ -383,6 +453,7 @@ alto_status alto_get_layout(alto_t t, int* nmodes, int* bits_per_mode, uint64_t*
       masks[2 * n + 1] = L.mask[n][1];
     }
     if (flag_bit) flag_bit[n] = L.flag_bit[n];
+    if (hot_bit) hot_bit[n] = L.hot_bit[n];
   }
   return ALTO_OK;
 }
@@ -416,6 +487,18 @@ alto_status alto_export(alto_t t, uint64_t* keys, uint32_t* perm, void* vals, in
     for (int64_t l = 0; l <= t->L; ++l) bounds[l] = seg_begin(l, t->M, t->L);
 done:
   return st;
+}
+
+alto_status alto_get_hot_rows(alto_t t, int mode, uint32_t* rows, int* count) {
+  if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
+  if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
+  if (count) *count = t->hot_n[mode];
+  if (rows && t->hot_n[mode] > 0) {
+    const cudaError_t e =
+        cudaMemcpy(rows, t->hot[mode], sizeof(uint32_t) * t->hot_n[mode], cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(ALTO_ECUDA, "hot rows: %s", cudaGetErrorString(e));
+  }
+  return ALTO_OK;
 }
 
 alto_status alto_set_variant(alto_t t, int mode, int variant) {

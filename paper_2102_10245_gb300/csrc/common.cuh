@@ -7,7 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/alto.h"
+#include "alto.h"
 
 namespace alto {
 
@@ -85,6 +85,17 @@ __device__ __forceinline__ uint32_t extract(const KeyT<KW>& k, const DecodeParam
 __host__ __device__ __forceinline__ int64_t seg_begin(int64_t l, int64_t M, int64_t L) {
   return static_cast<int64_t>(static_cast<uint64_t>(l) * static_cast<uint64_t>(M) /
                               static_cast<uint64_t>(L));
+}
+
+// Bit `bit` of a key (selects between the 32-bit words without indexing
+// the register array dynamically).
+template <int KW>
+__device__ __forceinline__ uint32_t key_bit(const KeyT<KW>& k, int bit) {
+  uint32_t w = k.w[0];
+#pragma unroll
+  for (int i = 1; i < 2 * KW; ++i)
+    if ((bit >> 5) == i) w = k.w[i];
+  return (w >> (bit & 31)) & 1u;
 }
 
 // ---------------------------------------------------------------------------

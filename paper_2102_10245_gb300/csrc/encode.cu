@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const uint64_t* __restrict__
 struct RowArrays {
   uint32_t* first[kMaxModes];
   uint32_t* last[kMaxModes];
+  uint32_t* cnt[kMaxModes];  // sampled nonzeros per row (every kHotSample-th)
 };
 
 // One warp per segment.  Lanes walk the segment, decode every mode, keep
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256) segment_stats_kernel(const __grid_constan
             if (ra.last[n] != nullptr) atomicMax(ra.last[n] + i, static_cast<uint32_t>(seg));
             prev[n] = i;
           }
+          if (ra.cnt[n] != nullptr && (x % kHotSample) == 0) atomicAdd(ra.cnt[n] + i, 1u);
         }
       }
     }
@@ -171,6 +173,8 @@ struct FlagParams {
   int nflag;
   int slot[kMaxModes];  // decode slot (= mode) of each flagged mode
   int bit[kMaxModes];   // key bit of its flag
+  int hot;              // 1: the flag marks a hot row (map lookup), 0: internal row
+  const uint32_t* map[kMaxModes];  // hot: bitmap of the mode's hot rows
 };
 
 template <int KW>
@@ -185,11 +189,49 @@ __global__ void __launch_bounds__(256) set_flags_kernel(const __grid_constant__ 
     for (int f = 0; f < fp.nflag; ++f) {
       const int n = fp.slot[f];
       const uint32_t i = extract<KW>(k, dp, n);
-      if (ra.first[n][i] == ra.last[n][i]) w[fp.bit[f] >> 6] |= 1ull << (fp.bit[f] & 63);
+      const bool set = fp.hot ? ((fp.map[f][i >> 5] >> (i & 31)) & 1u) != 0 : ra.first[n][i] == ra.last[n][i];
+      if (set) w[fp.bit[f] >> 6] |= 1ull << (fp.bit[f] & 63);
     }
     keys[x * KW] |= w[0];
     if (KW == 2) keys[x * KW + 1] |= w[1];
   }
+}
+
+// histogram of floor(log2(count)) over rows with a nonzero sampled count
+__global__ void __launch_bounds__(256) hot_hist_kernel(const uint32_t* __restrict__ cnt, uint64_t n,
+                                                       unsigned long long* hist) {
+  __shared__ unsigned long long h[33];
+  if (threadIdx.x < 33) h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t r = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const uint32_t c = cnt[r];
+    if (c) atomicAdd(&h[31 - __clz(c)], 1ull);
+  }
+  __syncthreads();
+  if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(hist + threadIdx.x, h[threadIdx.x]);
+}
+
+// append every row whose sampled count is >= thr as (count, row)
+__global__ void __launch_bounds__(256) hot_collect_kernel(const uint32_t* __restrict__ cnt, uint64_t n,
+                                                          uint32_t thr, uint32_t cap, uint32_t* out,
+                                                          uint32_t* out_n) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t r = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const uint32_t c = cnt[r];
+    if (c >= thr) {
+      const uint32_t k = atomicAdd(out_n, 1u);
+      if (k < cap) {
+        out[2 * k] = c;
+        out[2 * k + 1] = static_cast<uint32_t>(r);
+      }
+    }
+  }
+}
+
+__global__ void hot_map_kernel(const uint32_t* __restrict__ rows, int n, uint32_t* map) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicOr(map + (rows[i] >> 5), 1u << (rows[i] & 31));
 }
 
 unsigned grid_for(int64_t work, int per_block) {
@@ -261,9 +303,24 @@ cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dt
   return cudaGetLastError();
 }
 
+cudaError_t launch_hot_hist(const uint32_t* cnt, uint64_t n, unsigned long long* hist, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  hot_hist_kernel<<<grid_for(static_cast<int64_t>(n), 256 * 8), 256, 0, s>>>(cnt, n, hist);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hot_collect(const uint32_t* cnt, uint64_t n, uint32_t thr, uint32_t cap, uint32_t* out,
+                               uint32_t* out_n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  hot_collect_kernel<<<grid_for(static_cast<int64_t>(n), 256 * 8), 256, 0, s>>>(cnt, n, thr, cap, out, out_n);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_segment_stats(const Layout& lay, const uint64_t* keys, int64_t M, int64_t L,
                                  uint32_t* ivl, uint32_t* const* first, uint32_t* const* last,
-                                 cudaStream_t s) {
+                                 uint32_t* const* cnt, cudaStream_t s) {
   if (L <= 0) return cudaSuccess;
   DecodeParams dp;
   int ident[kMaxModes];
@@ -273,6 +330,7 @@ cudaError_t launch_segment_stats(const Layout& lay, const uint64_t* keys, int64_
   for (int n = 0; n < lay.N; ++n) {
     ra.first[n] = first[n];
     ra.last[n] = last[n];
+    ra.cnt[n] = cnt != nullptr ? cnt[n] : nullptr;
   }
   const unsigned g = grid_for(L, 8);
   if (lay.KW == 1)
@@ -299,15 +357,29 @@ cudaError_t launch_max_interval(const uint32_t* ivl, int64_t L, int N, unsigned 
   return cudaGetLastError();
 }
 
+cudaError_t launch_hot_map(const uint32_t* rows, int n, uint32_t* map, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  hot_map_kernel<<<(n + 255) / 256, 256, 0, s>>>(rows, n, map);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// One pass per kind of flag: the boundary / internal flags of Sec. 3.3
+// (hotmap == nullptr) or the hot-row flags (hotmap given per mode).
 cudaError_t launch_set_flags(const Layout& lay, uint64_t* keys, int64_t M,
-                             uint32_t* const* first, uint32_t* const* last, cudaStream_t s) {
+                             uint32_t* const* first, uint32_t* const* last,
+                             uint32_t* const* hotmap, cudaStream_t s) {
   FlagParams fp{};
-  for (int n = 0; n < lay.N; ++n)
-    if (lay.flag_bit[n] >= 0) {
+  fp.hot = hotmap != nullptr ? 1 : 0;
+  for (int n = 0; n < lay.N; ++n) {
+    const int b = fp.hot ? lay.hot_bit[n] : lay.flag_bit[n];
+    if (b >= 0 && (!fp.hot || hotmap[n] != nullptr)) {
       fp.slot[fp.nflag] = n;
-      fp.bit[fp.nflag] = lay.flag_bit[n];
+      fp.bit[fp.nflag] = b;
+      if (fp.hot) fp.map[fp.nflag] = hotmap[n];
       fp.nflag++;
     }
+  }
   if (fp.nflag == 0 || M <= 0) return cudaSuccess;
   DecodeParams dp;
   int ident[kMaxModes];

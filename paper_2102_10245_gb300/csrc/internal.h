@@ -22,6 +22,7 @@ struct Layout {
   int pos[kMaxModes][32] = {};     // key bit of bit l of mode n
   uint64_t mask[kMaxModes][2] = {};
   int flag_bit[kMaxModes] = {};    // -1: no helper flag for the mode
+  int hot_bit[kMaxModes] = {};     // -1: no hot-row flag for the mode
 };
 
 // Workspace of the CP-ALS driver, allocated on first use.
@@ -75,6 +76,10 @@ struct alto_tensor_s {
   uint32_t* perm = nullptr;   // M, input position of each nonzero
   void* vals = nullptr;       // M values in ALTO order
   uint32_t* ivl = nullptr;    // L x N x 2 closed intervals
+  uint32_t* hot[alto::kMaxModes] = {};  // hot rows per mode, hottest first
+  int hot_n[alto::kMaxModes] = {};
+  void* hot_rep = nullptr;              // MTTKRP hot-row replicas (lazy)
+  size_t hot_rep_bytes = 0;
   int* status = nullptr;      // device status word
   // statistics
   uint64_t distinct[alto::kMaxModes] = {};
@@ -150,15 +155,25 @@ cudaError_t launch_permute(const void* src, void* dst, const uint32_t* perm, int
                            int elem_bytes, cudaStream_t s);
 cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dtype vd, int64_t M,
                          double* out, cudaStream_t s);
+// Hot rows: every kHotSample-th nonzero is counted per row during the
+// segment statistics pass; the rows with the largest sampled counts (at most
+// kHotCap per mode) become the mode's hot list.
+constexpr int kHotSample = 16;
+constexpr int kHotCap = 1024;
 cudaError_t launch_segment_stats(const Layout& lay, const uint64_t* keys, int64_t M, int64_t L,
                                  uint32_t* ivl, uint32_t* const* first, uint32_t* const* last,
-                                 cudaStream_t s);
+                                 uint32_t* const* cnt, cudaStream_t s);
+cudaError_t launch_hot_hist(const uint32_t* cnt, uint64_t n, unsigned long long* hist, cudaStream_t s);
+cudaError_t launch_hot_collect(const uint32_t* cnt, uint64_t n, uint32_t thr, uint32_t cap, uint32_t* out,
+                               uint32_t* out_n, cudaStream_t s);
 cudaError_t launch_count_touched(const uint32_t* first, uint64_t n, unsigned long long* out,
                                  cudaStream_t s);
 cudaError_t launch_max_interval(const uint32_t* ivl, int64_t L, int N, unsigned long long* out,
                                 cudaStream_t s);
 cudaError_t launch_set_flags(const Layout& lay, uint64_t* keys, int64_t M,
-                             uint32_t* const* first, uint32_t* const* last, cudaStream_t s);
+                             uint32_t* const* first, uint32_t* const* last,
+                             uint32_t* const* hotmap, cudaStream_t s);
+cudaError_t launch_hot_map(const uint32_t* rows, int n, uint32_t* map, cudaStream_t s);
 
 // mttkrp.cu
 struct MttkrpLaunch;

@@ -62,6 +62,7 @@ alto_status make_layout(int N, const uint64_t* dims, int key_bits, Layout* out) 
     L.nbits[n] = bits_for_length(dims[n]);
     maxb = std::max(maxb, L.nbits[n]);
     L.flag_bit[n] = -1;
+    L.hot_bit[n] = -1;
   }
   int order[kMaxModes];
   for (int n = 0; n < N; ++n) order[n] = n;

@@ -10,6 +10,7 @@ namespace {
 
 constexpr size_t kSmemTempBytes = 96 * 1024;  // shared Temp budget per block
 
+
 int device_sms() {
   static int cached[64] = {};
   int dev = 0;
@@ -103,17 +104,49 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
   l.KW = lay.KW;
   l.sms = device_sms();
   if (v == ALTO_VAR_TEMP) return launch_temp_variant(t, l, fdtype, osz, s);
+  if (!mttkrp_specialised(N, R)) v = ALTO_VAR_ATOMIC;  // the generic kernel
   l.variant = v;
+  int H = 0;
+  if (v == ALTO_VAR_WARPAGG && lay.dims[mode] <= (1ull << 31) && mttkrp_specialised(N, R)) {
+    H = t->hot_n[mode];
+    if (H > 0) {
+      // replicas of the hot rows: kHotReplicas x kHotCap x R, kept in the handle
+      const size_t need = static_cast<size_t>(kHotReplicas) * kHotCap * R * osz;
+      if (t->hot_rep_bytes < need) {
+        dev_free(t, t->hot_rep);
+        t->hot_rep = dev_alloc(t, need);
+        t->hot_rep_bytes = t->hot_rep ? need : 0;
+        if (t->hot_rep == nullptr) return cudaErrorMemoryAllocation;
+      }
+      e = cudaMemsetAsync(t->hot_rep, 0, static_cast<size_t>(kHotReplicas) * H * R * osz, s);
+      if (e != cudaSuccess) return e;
+      int bits = 1;
+      while ((1 << bits) < 2 * H) ++bits;
+      l.args.hot = t->hot[mode];
+      l.args.hot_n = H;
+      l.args.hot_bits = bits;
+      l.args.hot_key_bit = lay.hot_bit[mode];
+      l.args.hot_rep = t->hot_rep;
+      l.smem_dyn = static_cast<size_t>(2) * (1u << bits) * sizeof(uint32_t);
+    }
+  }
   if (v == ALTO_VAR_SMEM) {
     const int rows = smem_rows_for(t, mode, R, osz);
     l.args.smem_rows = rows;
     l.smem_dyn = static_cast<size_t>(rows) * R * osz + static_cast<size_t>((rows + 31) / 32) * 4;
   }
-  switch (fdtype) {
-    case ALTO_F64: return mttkrp_dispatch_f64(l, s);
-    case ALTO_F32: return mttkrp_dispatch_f32(l, s);
-    default: return mttkrp_dispatch_bf16(l, s);
-  }
+  e = mttkrp_dispatch(l, fdtype, s);
+  if (e != cudaSuccess || H == 0) return e;
+  const int total = H * R;
+  const unsigned g = static_cast<unsigned>((total + 255) / 256);
+  if (osz == 8)
+    hot_reduce_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(t->hot_rep), t->hot[mode], H, R,
+                                                static_cast<double*>(out));
+  else
+    hot_reduce_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(t->hot_rep), t->hot[mode], H, R,
+                                               static_cast<float*>(out));
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace alto

@@ -1,0 +1,10 @@
+// Instantiation of the MTTKRP kernel family for __nv_bfloat16 factors and 2-word keys.
+#include "mttkrp_kernels.cuh"
+
+namespace alto {
+
+cudaError_t mttkrp_dispatch_bf16_k2(const MttkrpLaunch& l, cudaStream_t s) {
+  return mttkrp_dispatch_typed<__nv_bfloat16, 2>(l, s);
+}
+
+}  // namespace alto

@@ -1,0 +1,10 @@
+// Instantiation of the MTTKRP kernel family for float factors and 1-word keys.
+#include "mttkrp_kernels.cuh"
+
+namespace alto {
+
+cudaError_t mttkrp_dispatch_f32_k1(const MttkrpLaunch& l, cudaStream_t s) {
+  return mttkrp_dispatch_typed<float, 1>(l, s);
+}
+
+}  // namespace alto

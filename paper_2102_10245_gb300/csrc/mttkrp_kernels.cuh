@@ -1,60 +1,89 @@
 // MTTKRP over the ALTO format (Sec. 2.2, Alg. 1-2), GPU kernel family.
 //
-// Work split: the ordered nonzeros are cut into L equal-nnz line segments
-// (Sec. 3.2).  Every segment is processed by one warp, 32 nonzeros at a
-// time:
-//   1. each lane streams one key and value and de-linearizes all N indices
-//      (bit-level compress, EXTRACT of Alg. 2);
-//   2. the decoded tuples are staged in shared memory;
-//   3. lanes form groups of R/VEC lanes, a group owning one nonzero at a
-//      time and VEC consecutive columns per lane; each lane gathers its VEC
-//      columns of the N-1 input factor rows, multiplies them with the value
-//      (Hadamard product of Alg. 2) and accumulates into the output row.
+// Work split.  The ordered nonzeros are cut into L equal-nnz line segments
+// (Sec. 3.2); a thread block takes a unit of 8 consecutive segments, and its
+// 8 warps walk the unit in interleaved chunks of 32 nonzeros (warp w takes
+// chunks w, w+8, ...), so the rows a block touches at any moment come from a
+// short stretch of the line and stay in L1 / L2.  Per chunk:
+//   1. each lane de-linearizes one nonzero (bit-level compress per 32-bit key
+//      word, EXTRACT of Alg. 2); the next chunk's key and value are already
+//      being fetched;
+//   2. the decoded tuple (N indices + value) is staged in shared memory;
+//   3. groups of LPN lanes own one staged nonzero at a time, each lane CPL
+//      columns in 16-byte pieces; the gathers of the next position are
+//      issued before the current position's arithmetic (Hadamard product of
+//      the N-1 input rows, scaled by the value, packed FP32x2 math).
 //
-// Output accumulation variants (Alg. 2 and the Sec. 3.3 rule):
-//   ATOMIC  every nonzero issues a vector atomic into the output row (the
-//           ATOMIC branch of Alg. 2);
-//   WARPAGG the 32 staged nonzeros are reordered by output row inside the
-//           warp (match on the row, prefix over the matched sets) so that
-//           equal rows are consecutive; a group sums its run of an equal row
-//           in registers and issues one atomic per run;
-//   SMEM    a thread block takes 8 consecutive segments, sizes a Temp in
-//           shared memory by their output-mode interval T (Alg. 2, Temp_l),
-//           accumulates there with shared-memory atomics and then flushes
-//           every touched row once into the output; a block whose interval
-//           does not fit falls back to direct atomics.
-// All variants compute the same sum; only the rounding order differs.
+// Output accumulation policies (Alg. 2 and the Sec. 3.3 rule):
+//   ATOMIC  every nonzero adds its row into the output with vector atomics
+//           (the ATOMIC branch of Alg. 2);
+//   WARPAGG the chunk is reordered by output row inside the warp (match on
+//           the row, prefix over the matched sets) so equal rows are
+//           consecutive; a group sums a run in registers and adds it with one
+//           vector atomic.  Rows of the mode's hot list (the rows with the
+//           most nonzeros; their elements carry a hot flag in a spare key
+//           bit) are found in a shared-memory hash table while staging and
+//           added into one of kHotReplicas copies of the hot rows (chosen by
+//           block), which a small pass sums into the output afterwards: heavy
+//           rows no longer serialise on one L2 slice;
+//   SMEM    the unit's Temp lives in shared memory over the union of its
+//           segments' output-mode intervals (Temp_l of Alg. 2), filled with
+//           shared-memory atomics and flushed once per touched row; a unit
+//           whose interval does not fit falls back to WARPAGG;
+//   TEMP    as WARPAGG but into the unit's own Temp_u in device memory; a pull
+//           pass (mttkrp_temp.cu) then reduces the Temps into the output.
+// All policies compute the same sums; only the rounding order differs.
 #pragma once
 
 #include "internal.h"
 
 namespace alto {
 
+enum Policy { kAtomic = ALTO_VAR_ATOMIC, kWarpAgg = ALTO_VAR_WARPAGG, kSmem = ALTO_VAR_SMEM, kTemp = ALTO_VAR_TEMP };
+
 // ---------------------------------------------------------------------------
-// factor element traits: 16-byte vector loads of VEC elements
+// factor element traits: 16-byte loads of VEC elements, accumulation type AT
 template <typename FT>
 struct FTraits;
 template <>
 struct FTraits<float> {
   static constexpr int VEC = 4;
   using AT = float;
+  using VT = float;
 };
 template <>
 struct FTraits<double> {
   static constexpr int VEC = 2;
   using AT = double;
+  using VT = double;
 };
 template <>
 struct FTraits<__nv_bfloat16> {
   static constexpr int VEC = 8;
   using AT = float;
+  using VT = float;
+};
+
+// Column layout of one nonzero's row across its lane group: lane c of the
+// group owns the 16-byte pieces at columns c*VEC + q*STRIDE, q < PAIRS.  One
+// piece per lane up to 32 lanes keeps every warp-wide access at one L1
+// wavefront per row (the SM's L1 / shared path moves about 128 bytes per
+// clock, which bounds the gathers).
+template <int R, typename FT>
+struct Cols {
+  static constexpr int VEC = FTraits<FT>::VEC;
+  static constexpr int PAIRS = (R / VEC > 32) ? R / VEC / 32 : 1;
+  static constexpr int LPN = R / (VEC * PAIRS);  // lanes per nonzero
+  static constexpr int STRIDE = R / PAIRS;
+  static constexpr int CPL = VEC * PAIRS;        // columns per lane
+  static_assert(LPN >= 1 && LPN <= 32 && 32 % LPN == 0, "rank / vector width");
 };
 
 template <typename FT>
-__device__ __forceinline__ void load_vec(const FT* p, typename FTraits<FT>::AT* v);
+__device__ __forceinline__ void load16(const FT* p, typename FTraits<FT>::AT* v);
 
 template <>
-__device__ __forceinline__ void load_vec<float>(const float* p, float* v) {
+__device__ __forceinline__ void load16<float>(const float* p, float* v) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
   v[0] = a.x;
   v[1] = a.y;
@@ -63,14 +92,14 @@ __device__ __forceinline__ void load_vec<float>(const float* p, float* v) {
 }
 
 template <>
-__device__ __forceinline__ void load_vec<double>(const double* p, double* v) {
+__device__ __forceinline__ void load16<double>(const double* p, double* v) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(p));
   v[0] = a.x;
   v[1] = a.y;
 }
 
 template <>
-__device__ __forceinline__ void load_vec<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
   const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
   const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
@@ -83,232 +112,472 @@ __device__ __forceinline__ void load_vec<__nv_bfloat16>(const __nv_bfloat16* p, 
   }
 }
 
-// vector atomic add of VEC accumulators into out (FP32 or FP64)
+// elementwise helpers, packed FP32x2 where the accumulation type is float
+template <int K>
+__device__ __forceinline__ void scale_into(float* t, float v, const float* a) {
+  const float2 v2 = make_float2(v, v);
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r = __fmul2_rn(v2, make_float2(a[e], a[e + 1]));
+    t[e] = r.x;
+    t[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void scale_into(double* t, double v, const double* a) {
+#pragma unroll
+  for (int e = 0; e < K; ++e) t[e] = v * a[e];
+}
+template <int K>
+__device__ __forceinline__ void mul_into(float* t, const float* a) {
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r = __fmul2_rn(make_float2(t[e], t[e + 1]), make_float2(a[e], a[e + 1]));
+    t[e] = r.x;
+    t[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void mul_into(double* t, const double* a) {
+#pragma unroll
+  for (int e = 0; e < K; ++e) t[e] *= a[e];
+}
+template <int K>
+__device__ __forceinline__ void fma_into(float* acc, const float* t, const float* a) {
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r =
+        __ffma2_rn(make_float2(t[e], t[e + 1]), make_float2(a[e], a[e + 1]), make_float2(acc[e], acc[e + 1]));
+    acc[e] = r.x;
+    acc[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void fma_into(double* acc, const double* t, const double* a) {
+#pragma unroll
+  for (int e = 0; e < K; ++e) acc[e] = fma(t[e], a[e], acc[e]);
+}
+
+// VEC accumulators into global memory with vector atomics
 template <int VEC>
-__device__ __forceinline__ void atomic_vec(float* out, const float* v) {
+__device__ __forceinline__ void red_vec(float* out, const float* v) {
 #pragma unroll
   for (int j = 0; j < VEC; j += 4) red_add_v4(out + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
 }
 template <int VEC>
-__device__ __forceinline__ void atomic_vec(double* out, const double* v) {
+__device__ __forceinline__ void red_vec(double* out, const double* v) {
 #pragma unroll
   for (int j = 0; j < VEC; ++j) red_add_f64(out + j, v[j]);
 }
 
-template <typename AT>
-__device__ __forceinline__ AT load_val(const void* vals, int64_t x) {
-  return __ldcs(static_cast<const AT*>(vals) + x);
-}
-
 struct MttkrpArgs {
   const uint64_t* keys;
-  const void* vals;   // FP64 when the factors are FP64, else FP32
+  const void* vals;          // FP64 when the factors are FP64, else FP32
   int64_t M;
-  int64_t L;          // line segments
+  int64_t L;                 // line segments
   const void* f[kMaxModes];  // factor of each decode slot; slot N-1 is the output mode
   void* out;
   int R;
-  int out_mode;       // mode of the output (column of the interval table)
+  int out_mode;              // mode of the output (column of the interval table)
   const uint32_t* ivl;       // L x N x 2 segment intervals
-  int smem_rows;      // SMEM variant: rows of the shared Temp
+  int smem_rows;             // SMEM: rows of the shared Temp
+  void* temp;                // TEMP: all Temp_u back to back
+  const uint64_t* toff;      // TEMP: element offset of Temp_u
+  const uint32_t* ulo;       // TEMP: interval start of unit u
+  const uint32_t* hot;       // WARPAGG: hot rows of the output mode
+  int hot_n;                 // WARPAGG: hot rows in the table (0: none)
+  int hot_bits;              // WARPAGG: log2 of the hash table size
+  int hot_key_bit;           // WARPAGG: key bit flagging hot output rows, or -1
+  void* hot_rep;             // WARPAGG: kHotReplicas x hot_n x R accumulators
   DecodeParams dp;
 };
 
+constexpr uint32_t kHotEmpty = 0xffffffffu;
+constexpr int kHotReplicas = 32;  // copies of the hot rows (block b adds into copy b % 32)
+
+__device__ __forceinline__ uint32_t hot_hash(uint32_t row, int bits) {
+  return (row * 0x9E3779B1u) >> (32 - bits);
+}
+
+// slot of `row` in the block's hot table, or -1
+__device__ __forceinline__ int hot_lookup(const uint32_t* keys, const uint32_t* idx, uint32_t row, int bits) {
+  const uint32_t mask = (1u << bits) - 1u;
+  uint32_t h = hot_hash(row, bits);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {  // at most half full: an empty slot ends it early
+    const uint32_t k = keys[h];
+    if (k == row) return static_cast<int>(idx[h]);
+    if (k == kHotEmpty) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+constexpr int kUnitSegs = 8;  // segments per thread-block unit
 
-// ---------------------------------------------------------------------------
-// Decode one chunk of up to 32 nonzeros starting at `base` into shared
-// staging.  With AGG the chunk is reordered so equal output rows are
-// consecutive.  Returns the number of valid nonzeros.
-template <int N, int KW, typename AT, bool AGG>
-__device__ __forceinline__ int stage_chunk(const MttkrpArgs& a, int64_t base, int64_t end, int lane,
-                                           uint32_t (*s_idx)[32], AT* s_val) {
-  const int cnt = static_cast<int>(end - base < 32 ? end - base : 32);
-  const bool ok = lane < cnt;
-  uint32_t id[N];
-  AT v = AT(0);
-  if (ok) {
-    const KeyT<KW> k = load_key<KW>(a.keys, base + lane);
+// staged tuple: N indices and the value, padded to 16-byte words
+template <int N, typename VT>
+struct Stage {
+  static constexpr int WORDS_RAW = N + static_cast<int>(sizeof(VT) / 4);
+  static constexpr int W4 = (WORDS_RAW + 3) / 4;  // uint4 per entry
+};
+
+template <int N, typename VT>
+__device__ __forceinline__ void stage_store(uint4* slot, const uint32_t* id, VT v) {
+  uint32_t w[Stage<N, VT>::W4 * 4];
 #pragma unroll
-    for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
-    v = load_val<AT>(a.vals, base + lane);
-  }
-  int pos = lane;
-  if constexpr (AGG) {
-    const unsigned long long tag =
-        ok ? static_cast<unsigned long long>(id[N - 1]) : (0x100000000ull + lane);
-    const uint32_t peers = __match_any_sync(0xffffffffu, tag);
-    const int leader = __ffs(peers) - 1;
-    const uint32_t sz = (lane == leader) ? __popc(peers) : 0u;
-    uint32_t inc = sz;
+  for (int s = 0; s < N; ++s) w[s] = id[s];
+  memcpy(&w[N], &v, sizeof(VT));
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    const uint32_t start = __shfl_sync(0xffffffffu, inc - sz, leader);
-    pos = static_cast<int>(start + __popc(peers & lanemask_lt()));
-  }
-  if (ok) {
+  for (int s = N + static_cast<int>(sizeof(VT) / 4); s < Stage<N, VT>::W4 * 4; ++s) w[s] = 0;
 #pragma unroll
-    for (int s = 0; s < N; ++s) s_idx[s][pos] = id[s];
-    s_val[pos] = v;
-  }
-  __syncwarp();
-  return cnt;
+  for (int q = 0; q < Stage<N, VT>::W4; ++q) slot[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }
 
-// product v * prod_{s < N-1} U_s[i_s, cols] for one staged nonzero
-template <int N, int R, typename FT>
-__device__ __forceinline__ void nnz_product(const MttkrpArgs& a, const uint32_t (*s_idx)[32],
-                                            const typename FTraits<FT>::AT* s_val, int p, int c,
-                                            typename FTraits<FT>::AT* prod) {
-  using AT = typename FTraits<FT>::AT;
-  constexpr int VEC = FTraits<FT>::VEC;
-  const AT v = s_val[p];
+template <int N, typename VT>
+struct Pos {
+  uint32_t id[N];
+  VT v;
+};
+
+template <int N, typename VT>
+__device__ __forceinline__ Pos<N, VT> stage_load(const uint4* slot) {
+  uint32_t w[Stage<N, VT>::W4 * 4];
 #pragma unroll
-  for (int e = 0; e < VEC; ++e) prod[e] = v;
+  for (int q = 0; q < Stage<N, VT>::W4; ++q) {
+    const uint4 x = slot[q];
+    w[4 * q] = x.x;
+    w[4 * q + 1] = x.y;
+    w[4 * q + 2] = x.z;
+    w[4 * q + 3] = x.w;
+  }
+  Pos<N, VT> p;
+#pragma unroll
+  for (int s = 0; s < N; ++s) p.id[s] = w[s];
+  memcpy(&p.v, &w[N], sizeof(VT));
+  return p;
+}
+
+// gathered input rows of one position: (N-1) x CPL values
+template <int N, int R, typename FT>
+struct Rows {
+  typename FTraits<FT>::AT u[N > 1 ? N - 1 : 1][Cols<R, FT>::CPL];
+};
+
+template <int N, int R, typename FT, typename VT>
+__device__ __forceinline__ void gather(const MttkrpArgs& a, const Pos<N, VT>& p, int c, Rows<N, R, FT>& r) {
+  using C = Cols<R, FT>;
 #pragma unroll
   for (int s = 0; s < N - 1; ++s) {
-    const FT* row = static_cast<const FT*>(a.f[s]) + static_cast<size_t>(s_idx[s][p]) * R + c * VEC;
-    AT u[VEC];
-    load_vec<FT>(row, u);
+    const FT* row = static_cast<const FT*>(a.f[s]) + static_cast<size_t>(p.id[s]) * R + c * C::VEC;
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) prod[e] *= u[e];
+    for (int q = 0; q < C::PAIRS; ++q) load16<FT>(row + q * C::STRIDE, &r.u[s][q * C::VEC]);
   }
 }
 
-// ATOMIC (AGG = false) and WARPAGG (AGG = true)
-template <int N, int KW, int R, typename FT, bool AGG>
-__global__ void __launch_bounds__(kThreads) mttkrp_warp_kernel(const __grid_constant__ MttkrpArgs a) {
+// t = v * prod_s u_s
+template <int N, int R, typename FT, typename VT>
+__device__ __forceinline__ void product(const Pos<N, VT>& p, const Rows<N, R, FT>& r,
+                                        typename FTraits<FT>::AT* t) {
   using AT = typename FTraits<FT>::AT;
-  constexpr int VEC = FTraits<FT>::VEC;
-  constexpr int LPN = R / VEC;       // lanes per nonzero
-  constexpr int PER = LPN;           // staged positions per group (32 / groups)
-  static_assert(LPN >= 1 && LPN <= 32 && 32 % LPN == 0, "rank / vector width");
-  __shared__ uint32_t s_idx[kWarps][N][32];
-  __shared__ AT s_val[kWarps][32];
+  constexpr int K = Cols<R, FT>::CPL;
+  if constexpr (N == 1) {
+#pragma unroll
+    for (int e = 0; e < K; ++e) t[e] = static_cast<AT>(p.v);
+  } else {
+    scale_into<K>(t, static_cast<AT>(p.v), r.u[0]);
+#pragma unroll
+    for (int s = 1; s < N - 1; ++s) mul_into<K>(t, r.u[s]);
+  }
+}
+
+// acc += v * prod_s u_s
+template <int N, int R, typename FT, typename VT>
+__device__ __forceinline__ void accumulate(const Pos<N, VT>& p, const Rows<N, R, FT>& r,
+                                           typename FTraits<FT>::AT* acc) {
+  using AT = typename FTraits<FT>::AT;
+  constexpr int K = Cols<R, FT>::CPL;
+  AT t[K];
+  if constexpr (N <= 2) {
+    product<N, R, FT>(p, r, t);
+#pragma unroll
+    for (int e = 0; e < K; ++e) acc[e] += t[e];
+  } else {
+    scale_into<K>(t, static_cast<AT>(p.v), r.u[0]);
+#pragma unroll
+    for (int s = 1; s < N - 2; ++s) mul_into<K>(t, r.u[s]);
+    fma_into<K>(acc, t, r.u[N - 2]);
+  }
+}
+
+// flush a lane's CPL accumulators of one row into a dense row-major
+// destination (output or Temp) with vector atomics
+template <int R, typename FT>
+__device__ __forceinline__ void flush_global(typename FTraits<FT>::AT* rowp, int c,
+                                             const typename FTraits<FT>::AT* acc) {
+  using C = Cols<R, FT>;
+#pragma unroll
+  for (int q = 0; q < C::PAIRS; ++q) red_vec<C::VEC>(rowp + c * C::VEC + q * C::STRIDE, acc + q * C::VEC);
+}
+
+template <int R, typename FT>
+__device__ __forceinline__ void flush_shared(typename FTraits<FT>::AT* rowp, int c,
+                                             const typename FTraits<FT>::AT* acc) {
+  using C = Cols<R, FT>;
+#pragma unroll
+  for (int q = 0; q < C::PAIRS; ++q)
+#pragma unroll
+    for (int e = 0; e < C::VEC; ++e) atomicAdd(rowp + c * C::VEC + q * C::STRIDE + e, acc[q * C::VEC + e]);
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.
+template <int N, int KW, int R, typename FT, int POL>
+__global__ void __launch_bounds__(kThreads) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+  using AT = typename FTraits<FT>::AT;
+  using VT = typename FTraits<FT>::VT;
+  using C = Cols<R, FT>;
+  constexpr int LPN = C::LPN;
+  constexpr int PER = LPN;             // staged positions per group (32 / groups)
+  constexpr int K = C::CPL;
+  constexpr int W4 = Stage<N, VT>::W4;
+  constexpr bool AGG = POL != kAtomic;  // reorder by output row before the gathers
+  __shared__ uint4 s_stage[kWarps][32][W4];
+  __shared__ uint32_t s_lo, s_rows;
+  extern __shared__ __align__(16) unsigned char dyn[];
+
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / LPN, c = lane % LPN;
+  const uint32_t lt = lanemask_lt();
   AT* out = static_cast<AT*>(a.out);
-  const int64_t nw = static_cast<int64_t>(gridDim.x) * kWarps;
-  for (int64_t seg = static_cast<int64_t>(blockIdx.x) * kWarps + warp; seg < a.L; seg += nw) {
-    const int64_t s0 = seg_begin(seg, a.M, a.L), s1 = seg_begin(seg + 1, a.M, a.L);
-    for (int64_t base = s0; base < s1; base += 32) {
-      const int cnt = stage_chunk<N, KW, AT, AGG>(a, base, s1, lane, s_idx[warp], s_val[warp]);
-      AT acc[VEC];
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) acc[e] = AT(0);
-#pragma unroll 2
-      for (int j = 0; j < PER; ++j) {
-        const int p = g * PER + j;
-        if (p >= cnt) break;
-        const uint32_t row = s_idx[warp][N - 1][p];
-        AT prod[VEC];
-        nnz_product<N, R, FT>(a, s_idx[warp], s_val[warp], p, c, prod);
-        if constexpr (AGG) {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) acc[e] += prod[e];
-          const bool last = (j == PER - 1) || (p + 1 >= cnt) || (s_idx[warp][N - 1][p + 1] != row);
-          if (last) {
-            atomic_vec<VEC>(out + static_cast<size_t>(row) * R + c * VEC, acc);
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) acc[e] = AT(0);
+  const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
+
+  // WARPAGG: the block's hot-row table (keys, slot index) and its replica
+  int H = 0;
+  AT* hdata = nullptr;
+  uint32_t* hkeys = nullptr;
+  uint32_t* hidx = nullptr;
+  if constexpr (POL == kWarpAgg) {
+    H = a.hot_n;
+    if (H > 0) {
+      const int TS = 1 << a.hot_bits;
+      hdata = static_cast<AT*>(a.hot_rep) + static_cast<size_t>(blockIdx.x % kHotReplicas) * H * R;
+      hkeys = reinterpret_cast<uint32_t*>(dyn);
+      hidx = hkeys + TS;
+      for (int i = threadIdx.x; i < TS; i += kThreads) hkeys[i] = kHotEmpty;
+      __syncthreads();
+      const uint32_t mask = static_cast<uint32_t>(TS - 1);
+      for (int i = threadIdx.x; i < H; i += kThreads) {
+        const uint32_t row = a.hot[i];
+        uint32_t h = hot_hash(row, a.hot_bits);
+        for (int probe = 0; probe < TS; ++probe) {
+          if (atomicCAS(hkeys + h, kHotEmpty, row) == kHotEmpty) {
+            hidx[h] = static_cast<uint32_t>(i);
+            break;
           }
-        } else {
-          atomic_vec<VEC>(out + static_cast<size_t>(row) * R + c * VEC, prod);
+          h = (h + 1) & mask;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t useg1 = (u + 1) * kUnitSegs < a.L ? (u + 1) * kUnitSegs : a.L;
+    const int64_t ub = seg_begin(u * kUnitSegs, a.M, a.L), ue = seg_begin(useg1, a.M, a.L);
+
+    // destination of this unit
+    AT* dst = out;
+    uint32_t lo = 0;
+    bool use_smem = false;
+    if constexpr (POL == kSmem) {
+      if (warp == 0) {
+        const int64_t seg = u * kUnitSegs + lane;
+        uint32_t l0 = 0xffffffffu, h0 = 0;
+        if (lane < kUnitSegs && seg < a.L) {
+          const int Nm = a.dp.nmodes;
+          const uint32_t s0 = a.ivl[(seg * Nm + a.out_mode) * 2], e0 = a.ivl[(seg * Nm + a.out_mode) * 2 + 1];
+          if (e0 >= s0) {
+            l0 = s0;
+            h0 = e0;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          l0 = min(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+          h0 = max(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+        }
+        if (lane == 0) {
+          s_lo = l0;
+          s_rows = (h0 >= l0) ? h0 - l0 + 1 : 0;
+        }
+      }
+      __syncthreads();
+      lo = s_lo;
+      const uint32_t rows = s_rows;
+      use_smem = rows <= static_cast<uint32_t>(a.smem_rows);
+      if (use_smem) {
+        AT* temp = reinterpret_cast<AT*>(dyn);
+        uint32_t* touched = reinterpret_cast<uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
+        for (uint32_t i = threadIdx.x; i < rows * R; i += kThreads) temp[i] = AT(0);
+        for (uint32_t i = threadIdx.x; i < (rows + 31) / 32; i += kThreads) touched[i] = 0;
+        dst = temp;
+      }
+      __syncthreads();
+    } else if constexpr (POL == kTemp) {
+      dst = static_cast<AT*>(a.temp) + a.toff[u];
+      lo = a.ulo[u];
+    }
+
+    // chunks of this unit: warp w takes w, w + 8, ...
+    int64_t base = ub + static_cast<int64_t>(warp) * 32;
+    KeyT<KW> kn{};
+    VT vn = VT(0);
+    if (base + lane < ue) {
+      kn = load_key<KW>(a.keys, base + lane);
+      vn = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
+    }
+    for (; base < ue; base += kWarps * 32) {
+      const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
+      const bool ok = lane < cnt;
+      const KeyT<KW> k = kn;
+      const VT v = vn;
+      const int64_t nb = base + kWarps * 32;
+      if (nb + lane < ue) {  // prefetch the warp's next chunk
+        kn = load_key<KW>(a.keys, nb + lane);
+        vn = __ldcs(static_cast<const VT*>(a.vals) + nb + lane);
+      }
+      uint32_t id[N];
+#pragma unroll
+      for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
+      if constexpr (POL == kWarpAgg) {
+        // hot rows are staged as (bit 31 | table slot); the host enables the
+        // table only when every output row is below 2^31.  Only nonzeros
+        // whose key carries the hot-row flag probe the table.
+        if (H > 0 && ok && (a.hot_key_bit < 0 || key_bit<KW>(k, a.hot_key_bit))) {
+          const int slot = hot_lookup(hkeys, hidx, id[N - 1], a.hot_bits);
+          if (slot >= 0) id[N - 1] = 0x80000000u | static_cast<uint32_t>(slot);
+        }
+      }
+      int pos = lane;
+      if constexpr (AGG) {
+        const unsigned long long tag = ok ? static_cast<unsigned long long>(id[N - 1]) : (0x100000000ull + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+        const int leader = __ffs(peers) - 1;
+        const uint32_t sz = (lane == leader) ? __popc(peers) : 0u;
+        uint32_t inc = sz;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const uint32_t start = __shfl_sync(0xffffffffu, inc - sz, leader);
+        pos = static_cast<int>(start + __popc(peers & lt));
+      }
+      if (ok) stage_store<N, VT>(s_stage[warp][pos], id, v);
+      __syncwarp();
+
+      // group g: positions g*PER .. g*PER + PER - 1, gathers one position
+      // ahead.  Loads past the chunk's end read its last valid slot again
+      // (harmless, the result is not used), so every load is unconditional
+      // and the pipeline registers rename instead of being copied.
+      const int p0 = g * PER;
+      Pos<N, VT> cur = stage_load<N, VT>(s_stage[warp][p0 < cnt ? p0 : cnt - 1]);
+      Rows<N, R, FT> rc;
+      gather<N, R, FT>(a, cur, c, rc);
+      AT acc[K];
+#pragma unroll
+      for (int e = 0; e < K; ++e) acc[e] = AT(0);
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int p = p0 + j;
+        const bool has = p < cnt;
+        const bool hasn = (j + 1 < PER) && (p + 1 < cnt);
+        Pos<N, VT> nxt;
+        Rows<N, R, FT> rn;
+        if (j + 1 < PER) {
+          nxt = stage_load<N, VT>(s_stage[warp][p + 1 < cnt ? p + 1 : cnt - 1]);
+          gather<N, R, FT>(a, nxt, c, rn);
+        }
+        if (has) {
+          const uint32_t row = cur.id[N - 1];
+          if constexpr (POL == kAtomic) {
+            AT t[K];
+            product<N, R, FT>(cur, rc, t);
+            flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, t);
+          } else {
+            accumulate<N, R, FT>(cur, rc, acc);
+            if (!hasn || nxt.id[N - 1] != row) {
+              if constexpr (POL == kSmem) {
+                if (use_smem) {
+                  flush_shared<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
+                  if (c == 0) {
+                    uint32_t* touched = reinterpret_cast<uint32_t*>(reinterpret_cast<AT*>(dyn) +
+                                                                    static_cast<size_t>(a.smem_rows) * R);
+                    atomicOr(touched + ((row - lo) >> 5), 1u << ((row - lo) & 31));
+                  }
+                } else {
+                  flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
+                }
+              } else if constexpr (POL == kWarpAgg) {
+                if (row & 0x80000000u)
+                  flush_global<R, FT>(hdata + static_cast<size_t>(row & 0x7fffffffu) * R, c, acc);
+                else
+                  flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
+              } else {
+                flush_global<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
+              }
+#pragma unroll
+              for (int e = 0; e < K; ++e) acc[e] = AT(0);
+            }
+          }
+        }
+        if (j + 1 < PER) {
+          cur = nxt;
+          rc = rn;
         }
       }
       __syncwarp();
     }
-  }
-}
 
-// SMEM: 8 segments per block, Temp in shared memory over the union of their
-// output-mode intervals; direct atomics when the interval is too wide.
-template <int N, int KW, int R, typename FT>
-__global__ void __launch_bounds__(kThreads) mttkrp_smem_kernel(const __grid_constant__ MttkrpArgs a) {
-  using AT = typename FTraits<FT>::AT;
-  constexpr int VEC = FTraits<FT>::VEC;
-  constexpr int LPN = R / VEC;
-  constexpr int PER = LPN;
-  __shared__ uint32_t s_idx[kWarps][N][32];
-  __shared__ AT s_val[kWarps][32];
-  __shared__ uint32_t s_lo, s_rows;
-  extern __shared__ __align__(16) unsigned char dyn[];
-  AT* temp = reinterpret_cast<AT*>(dyn);
-  uint32_t* touched = reinterpret_cast<uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane / LPN, c = lane % LPN;
-  AT* out = static_cast<AT*>(a.out);
-  const int64_t units = (a.L + kWarps - 1) / kWarps;
-  const int Nm = a.dp.nmodes;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    if (warp == 0) {
-      const int64_t seg = u * kWarps + lane;
-      uint32_t lo = 0xffffffffu, hi = 0;
-      if (lane < kWarps && seg < a.L) {
-        const uint32_t s = a.ivl[(seg * Nm + a.out_mode) * 2], e = a.ivl[(seg * Nm + a.out_mode) * 2 + 1];
-        if (e >= s) {
-          lo = s;
-          hi = e;
-        }
-      }
+    if constexpr (POL == kSmem) {
+      __syncthreads();
+      if (use_smem) {
+        const AT* temp = reinterpret_cast<const AT*>(dyn);
+        const uint32_t* touched = reinterpret_cast<const uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
+        const uint32_t rows = s_rows;
+        const int cc = threadIdx.x % LPN;
+        for (uint32_t w = threadIdx.x / LPN; w < rows; w += kThreads / LPN) {
+          if ((touched[w >> 5] >> (w & 31)) & 1u) {
+            AT vals[K];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-      }
-      if (lane == 0) {
-        s_lo = lo;
-        s_rows = (hi >= lo) ? hi - lo + 1 : 0;
-      }
-    }
-    __syncthreads();
-    const uint32_t lo = s_lo, rows = s_rows;
-    const bool fits = rows <= static_cast<uint32_t>(a.smem_rows);
-    if (fits) {
-      for (uint32_t i = threadIdx.x; i < rows * R; i += kThreads) temp[i] = AT(0);
-      for (uint32_t i = threadIdx.x; i < (rows + 31) / 32; i += kThreads) touched[i] = 0;
-    }
-    __syncthreads();
-    const int64_t seg = u * kWarps + warp;
-    if (seg < a.L) {
-      const int64_t s0 = seg_begin(seg, a.M, a.L), s1 = seg_begin(seg + 1, a.M, a.L);
-      for (int64_t base = s0; base < s1; base += 32) {
-        const int cnt = stage_chunk<N, KW, AT, false>(a, base, s1, lane, s_idx[warp], s_val[warp]);
-#pragma unroll 2
-        for (int j = 0; j < PER; ++j) {
-          const int p = g * PER + j;
-          if (p >= cnt) break;
-          const uint32_t row = s_idx[warp][N - 1][p];
-          AT prod[VEC];
-          nnz_product<N, R, FT>(a, s_idx[warp], s_val[warp], p, c, prod);
-          if (fits) {
-            AT* t = temp + static_cast<size_t>(row - lo) * R + c * VEC;
+            for (int q = 0; q < C::PAIRS; ++q)
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) atomicAdd(t + e, prod[e]);
-            if (c == 0) atomicOr(touched + ((row - lo) >> 5), 1u << ((row - lo) & 31));
-          } else {
-            atomic_vec<VEC>(out + static_cast<size_t>(row) * R + c * VEC, prod);
+              for (int e = 0; e < C::VEC; ++e)
+                vals[q * C::VEC + e] = temp[static_cast<size_t>(w) * R + cc * C::VEC + q * C::STRIDE + e];
+            flush_global<R, FT>(out + static_cast<size_t>(lo + w) * R, cc, vals);
           }
         }
-        __syncwarp();
       }
+      __syncthreads();
     }
-    __syncthreads();
-    if (fits) {
-      // flush: one vector atomic per (touched row, lane slot)
-      for (uint32_t w = threadIdx.x / LPN; w < rows; w += kThreads / LPN) {
-        if ((touched[w >> 5] >> (w & 31)) & 1u) {
-          const int cc = threadIdx.x % LPN;
-          atomic_vec<VEC>(out + static_cast<size_t>(lo + w) * R + cc * VEC,
-                          temp + static_cast<size_t>(w) * R + cc * VEC);
-        }
-      }
-    }
-    __syncthreads();
+  }
+
+}
+
+// out[hot[h], :] = sum over the replicas of rep[k, h, :] (every contribution
+// to a row in the hot table went to the replicas, none to the output)
+template <typename AT>
+__global__ void __launch_bounds__(256) hot_reduce_kernel(const AT* __restrict__ rep, const uint32_t* __restrict__ hot,
+                                                         int H, int R, AT* __restrict__ out) {
+  const int total = H * R;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    AT s = AT(0);
+#pragma unroll 8
+    for (int k = 0; k < kHotReplicas; ++k) s += rep[static_cast<size_t>(k) * total + e];
+    const int h = e / R, r = e - h * R;
+    out[static_cast<size_t>(hot[h]) * R + r] = s;
   }
 }
 
@@ -317,8 +586,9 @@ __global__ void __launch_bounds__(kThreads) mttkrp_smem_kernel(const __grid_cons
 template <int KW, typename FT>
 __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
+  using VT = typename FTraits<FT>::VT;
   __shared__ uint32_t s_idx[kWarps][kMaxModes][32];
-  __shared__ AT s_val[kWarps][32];
+  __shared__ VT s_val[kWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int Nm = a.dp.nmodes, R = a.R;
   AT* out = static_cast<AT*>(a.out);
@@ -330,13 +600,13 @@ __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_c
       if (lane < cnt) {
         const KeyT<KW> k = load_key<KW>(a.keys, base + lane);
         for (int s = 0; s < Nm; ++s) s_idx[warp][s][lane] = extract<KW>(k, a.dp, s);
-        s_val[warp][lane] = load_val<AT>(a.vals, base + lane);
+        s_val[warp][lane] = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
       }
       __syncwarp();
       for (int p = 0; p < cnt; ++p) {
         const uint32_t row = s_idx[warp][Nm - 1][p];
         for (int r = lane; r < R; r += 32) {
-          AT t = s_val[warp][p];
+          AT t = static_cast<AT>(s_val[warp][p]);
           for (int s = 0; s < Nm - 1; ++s) {
             const FT* f = static_cast<const FT*>(a.f[s]);
             t *= static_cast<AT>(f[static_cast<size_t>(s_idx[warp][s][p]) * R + r]);
@@ -355,19 +625,30 @@ struct MttkrpLaunch {
   MttkrpArgs args;
   int N;
   int KW;
-  int variant;   // ALTO_VAR_ATOMIC / WARPAGG / SMEM (the generic kernel ignores it)
+  int variant;   // ATOMIC / WARPAGG / SMEM / TEMP (the generic kernel ignores it)
   int sms;       // SM count of the device
   size_t smem_dyn;
 };
 
-cudaError_t mttkrp_dispatch_f32(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_f64(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_bf16(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_f32_k1(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_f32_k2(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_f64_k1(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_f64_k2(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_bf16_k1(const MttkrpLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_dispatch_bf16_k2(const MttkrpLaunch& l, cudaStream_t s);
+
+inline cudaError_t mttkrp_dispatch(const MttkrpLaunch& l, alto_dtype fdtype, cudaStream_t s) {
+  switch (fdtype) {
+    case ALTO_F64: return l.KW == 1 ? mttkrp_dispatch_f64_k1(l, s) : mttkrp_dispatch_f64_k2(l, s);
+    case ALTO_F32: return l.KW == 1 ? mttkrp_dispatch_f32_k1(l, s) : mttkrp_dispatch_f32_k2(l, s);
+    default: return l.KW == 1 ? mttkrp_dispatch_bf16_k1(l, s) : mttkrp_dispatch_bf16_k2(l, s);
+  }
+}
 
 // Persistent launch: as many blocks as fit on the device at once (never more
 // than the work units), each striding over the units.
 template <typename Kern>
-cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, cudaStream_t s) {
+cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, int64_t units, cudaStream_t s) {
   if (smem > 48 * 1024) {
     const cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -377,7 +658,6 @@ cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, cud
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
-  const int64_t units = (l.args.L + kWarps - 1) / kWarps;
   int64_t g = static_cast<int64_t>(l.sms) * occ;
   if (g > units) g = units;
   if (g < 1) g = 1;
@@ -386,51 +666,40 @@ cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, cud
   return cudaGetLastError();
 }
 
-// Instantiate and launch for one factor type.
-template <typename FT>
-cudaError_t mttkrp_dispatch(const MttkrpLaunch& l, cudaStream_t s) {
+// Instantiate and launch for one factor type and key width.
+template <typename FT, int KW>
+cudaError_t mttkrp_dispatch_typed(const MttkrpLaunch& l, cudaStream_t s) {
   const MttkrpArgs& a = l.args;
-#define ALTO_LAUNCH_NR(NN, KK, RR)                                                           \
-  do {                                                                                      \
-    if (l.variant == ALTO_VAR_SMEM)                                                         \
-      return launch_persistent(mttkrp_smem_kernel<NN, KK, RR, FT>, l, l.smem_dyn, s);       \
-    if (l.variant == ALTO_VAR_WARPAGG)                                                      \
-      return launch_persistent(mttkrp_warp_kernel<NN, KK, RR, FT, true>, l, 0, s);          \
-    return launch_persistent(mttkrp_warp_kernel<NN, KK, RR, FT, false>, l, 0, s);           \
+  const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
+#define ALTO_LAUNCH_NR(NN, RR)                                                                           \
+  do {                                                                                                   \
+    switch (l.variant) {                                                                                 \
+      case kSmem: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kSmem>, l, l.smem_dyn, units, s); \
+      case kTemp: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kTemp>, l, 0, units, s);        \
+      case kWarpAgg: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg>, l, l.smem_dyn, units, s); \
+      default: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic>, l, 0, units, s);         \
+    }                                                                                                    \
   } while (0)
-#define ALTO_LAUNCH_R(NN, KK)              \
-  do {                                     \
-    switch (a.R) {                         \
-      case 8: ALTO_LAUNCH_NR(NN, KK, 8);   \
-      case 16: ALTO_LAUNCH_NR(NN, KK, 16); \
-      case 32: ALTO_LAUNCH_NR(NN, KK, 32); \
-      case 64: ALTO_LAUNCH_NR(NN, KK, 64); \
-      default: break;                      \
-    }                                      \
+#define ALTO_LAUNCH_R(NN)              \
+  do {                                 \
+    switch (a.R) {                     \
+      case 8: ALTO_LAUNCH_NR(NN, 8);   \
+      case 16: ALTO_LAUNCH_NR(NN, 16); \
+      case 32: ALTO_LAUNCH_NR(NN, 32); \
+      case 64: ALTO_LAUNCH_NR(NN, 64); \
+      default: break;                  \
+    }                                  \
   } while (0)
-#define ALTO_LAUNCH_N(KK)           \
-  do {                              \
-    switch (l.N) {                  \
-      case 2: ALTO_LAUNCH_R(2, KK); \
-        break;                      \
-      case 3: ALTO_LAUNCH_R(3, KK); \
-        break;                      \
-      case 4: ALTO_LAUNCH_R(4, KK); \
-        break;                      \
-      case 5: ALTO_LAUNCH_R(5, KK); \
-        break;                      \
-      default: break;               \
-    }                               \
-  } while (0)
-  if (l.KW == 1) {
-    ALTO_LAUNCH_N(1);
-    return launch_persistent(mttkrp_generic_kernel<1, FT>, l, 0, s);
+  switch (l.N) {
+    case 2: ALTO_LAUNCH_R(2); break;
+    case 3: ALTO_LAUNCH_R(3); break;
+    case 4: ALTO_LAUNCH_R(4); break;
+    case 5: ALTO_LAUNCH_R(5); break;
+    default: break;
   }
-  ALTO_LAUNCH_N(2);
-  return launch_persistent(mttkrp_generic_kernel<2, FT>, l, 0, s);
-#undef ALTO_LAUNCH_N
 #undef ALTO_LAUNCH_R
 #undef ALTO_LAUNCH_NR
+  return launch_persistent(mttkrp_generic_kernel<KW, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
 }
 
 // Whether the specialised kernels cover (N, R); otherwise the generic one runs.

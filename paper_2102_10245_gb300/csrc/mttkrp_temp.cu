@@ -4,7 +4,8 @@
 //   accumulate: thread-block unit u (8 consecutive line segments) adds every
 //               nonzero's contribution into its own Temp_u, a dense block of
 //               (hi_u - lo_u + 1) x R elements over the unit's output-mode
-//               interval [lo_u, hi_u] (Temp_l(i - T^s_l, r) in Alg. 2);
+//               interval [lo_u, hi_u] (Temp_l(i - T^s_l, r) in Alg. 2); this
+//               is the TEMP policy of the kernel in mttkrp_kernels.cuh;
 //   pull:       every output row b sums Temp_u(b - lo_u, :) over the units
 //               whose interval contains b (the pull-based reduction of
 //               Alg. 2), in unit order.
@@ -19,55 +20,6 @@
 namespace alto {
 
 namespace {
-
-struct TempArgs {
-  void* temp;
-  const uint64_t* toff;
-  const uint32_t* ulo;
-};
-
-template <int N, int KW, int R, typename FT>
-__global__ void __launch_bounds__(kThreads) mttkrp_temp_kernel(const __grid_constant__ MttkrpArgs a,
-                                                               const __grid_constant__ TempArgs ta) {
-  using AT = typename FTraits<FT>::AT;
-  constexpr int VEC = FTraits<FT>::VEC;
-  constexpr int LPN = R / VEC;
-  constexpr int PER = LPN;
-  __shared__ uint32_t s_idx[kWarps][N][32];
-  __shared__ AT s_val[kWarps][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane / LPN, c = lane % LPN;
-  const int64_t units = (a.L + kWarps - 1) / kWarps;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    AT* tu = static_cast<AT*>(ta.temp) + ta.toff[u];
-    const uint32_t lo = ta.ulo[u];
-    const int64_t seg = u * kWarps + warp;
-    if (seg >= a.L) continue;
-    const int64_t s0 = seg_begin(seg, a.M, a.L), s1 = seg_begin(seg + 1, a.M, a.L);
-    for (int64_t base = s0; base < s1; base += 32) {
-      const int cnt = stage_chunk<N, KW, AT, true>(a, base, s1, lane, s_idx[warp], s_val[warp]);
-      AT acc[VEC];
-#pragma unroll
-      for (int e = 0; e < VEC; ++e) acc[e] = AT(0);
-      for (int j = 0; j < PER; ++j) {
-        const int p = g * PER + j;
-        if (p >= cnt) break;
-        const uint32_t row = s_idx[warp][N - 1][p];
-        AT prod[VEC];
-        nnz_product<N, R, FT>(a, s_idx[warp], s_val[warp], p, c, prod);
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[e] += prod[e];
-        const bool last = (j == PER - 1) || (p + 1 >= cnt) || (s_idx[warp][N - 1][p + 1] != row);
-        if (last) {
-          atomic_vec<VEC>(tu + static_cast<size_t>(row - lo) * R + c * VEC, acc);
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) acc[e] = AT(0);
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
 
 template <typename AT>
 __global__ void __launch_bounds__(256) temp_pull_kernel(const AT* __restrict__ temp,
@@ -89,54 +41,6 @@ __global__ void __launch_bounds__(256) temp_pull_kernel(const AT* __restrict__ t
     }
     out[e] = s;
   }
-}
-
-template <typename FT>
-cudaError_t temp_dispatch(const MttkrpLaunch& l, const TempArgs& ta, cudaStream_t s) {
-  const MttkrpArgs& a = l.args;
-  int64_t units = (a.L + kWarps - 1) / kWarps;
-  int64_t g = static_cast<int64_t>(l.sms) * 8;
-  if (g > units) g = units;
-  if (g < 1) g = 1;
-  const unsigned grid = static_cast<unsigned>(g);
-#define ALTO_TEMP_NR(NN, KK, RR)                                             \
-  do {                                                                       \
-    mttkrp_temp_kernel<NN, KK, RR, FT><<<grid, kThreads, 0, s>>>(a, ta);     \
-    note_launch();                                                           \
-    return cudaGetLastError();                                               \
-  } while (0)
-#define ALTO_TEMP_R(NN, KK)              \
-  do {                                   \
-    switch (a.R) {                       \
-      case 8: ALTO_TEMP_NR(NN, KK, 8);   \
-      case 16: ALTO_TEMP_NR(NN, KK, 16); \
-      case 32: ALTO_TEMP_NR(NN, KK, 32); \
-      case 64: ALTO_TEMP_NR(NN, KK, 64); \
-      default: break;                    \
-    }                                    \
-  } while (0)
-#define ALTO_TEMP_N(KK)           \
-  do {                            \
-    switch (l.N) {                \
-      case 2: ALTO_TEMP_R(2, KK); \
-        break;                    \
-      case 3: ALTO_TEMP_R(3, KK); \
-        break;                    \
-      case 4: ALTO_TEMP_R(4, KK); \
-        break;                    \
-      case 5: ALTO_TEMP_R(5, KK); \
-        break;                    \
-      default: break;             \
-    }                             \
-  } while (0)
-  if (l.KW == 1)
-    ALTO_TEMP_N(1);
-  else
-    ALTO_TEMP_N(2);
-#undef ALTO_TEMP_N
-#undef ALTO_TEMP_R
-#undef ALTO_TEMP_NR
-  return cudaErrorInvalidValue;  // not specialised: caller falls back
 }
 
 }  // namespace
@@ -219,21 +123,16 @@ cudaError_t launch_temp_variant(alto_tensor_s* t, const MttkrpLaunch& l, alto_dt
   MttkrpLaunch fb = l;
   if (!p.feasible || !mttkrp_specialised(l.N, R)) {
     // Temp too large (or no specialised kernel): warp aggregation instead
-    fb.variant = ALTO_VAR_WARPAGG;
-    switch (fdtype) {
-      case ALTO_F64: return mttkrp_dispatch_f64(fb, s);
-      case ALTO_F32: return mttkrp_dispatch_f32(fb, s);
-      default: return mttkrp_dispatch_bf16(fb, s);
-    }
+    fb.variant = mttkrp_specialised(l.N, R) ? ALTO_VAR_WARPAGG : ALTO_VAR_ATOMIC;
+    return mttkrp_dispatch(fb, fdtype, s);
   }
   cudaError_t e = cudaMemsetAsync(p.temp, 0, p.temp_elems * osz, s);
   if (e != cudaSuccess) return e;
-  TempArgs ta{p.temp, p.toff, p.ulo};
-  switch (fdtype) {
-    case ALTO_F64: e = temp_dispatch<double>(l, ta, s); break;
-    case ALTO_F32: e = temp_dispatch<float>(l, ta, s); break;
-    default: e = temp_dispatch<__nv_bfloat16>(l, ta, s); break;
-  }
+  fb.variant = ALTO_VAR_TEMP;
+  fb.args.temp = p.temp;
+  fb.args.toff = p.toff;
+  fb.args.ulo = p.ulo;
+  e = mttkrp_dispatch(fb, fdtype, s);
   if (e != cudaSuccess) return e;
   const uint64_t I = t->lay.dims[mode];
   const uint64_t total = I * static_cast<uint64_t>(R);

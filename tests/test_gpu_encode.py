@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def _flag_mask(lay):
     lo = hi = 0
-    for b in lay["flag_bit"]:
+    for b in list(lay["flag_bit"]) + list(lay["hot_bit"]):
         if b >= 0:
             if b < 64:
                 lo |= 1 << b
@@ -50,7 +50,40 @@ def check_format(dims, idx, vals, at):
             got = (word >> np.uint64(b % 64)) & np.uint64(1)
             ref = oracle.flags(o["coords"], dims[n], n, o["bounds"])
             assert (got.astype(np.uint8) == ref).all(), "flags differ in mode %d" % n
+        check_hot(at, n, o["coords"][:, n].astype(np.int64), lay, ex["keys"], dims[n])
     return ex, o
+
+
+def expected_hot_rows(rows_in_alto_order, I):
+    """The hot-row rule: count every 16th nonzero in ALTO order per row; keep
+    the rows whose count reaches the smallest power of two 2^b (b >= 1) that
+    leaves at most 1024 rows; hottest first, ties by row."""
+    c = np.bincount(rows_in_alto_order[::16], minlength=I)
+    nz = c[c > 0]
+    if nz.size == 0:
+        return np.zeros(0, np.int64)
+    lg = np.floor(np.log2(nz)).astype(np.int64)
+    hist = np.bincount(lg, minlength=33)
+    b = 1
+    above = hist[1:].sum()
+    while b < 33 and above > 1024:
+        above -= hist[b]
+        b += 1
+    if b >= 33 or above == 0:
+        return np.zeros(0, np.int64)
+    rows = np.flatnonzero(c >= (1 << b))
+    order = np.lexsort((rows, -c[rows]))
+    return rows[order]
+
+
+def check_hot(at, n, rows_sorted, lay, keys, I):
+    hot = at.hot_rows(n).astype(np.int64)
+    assert (hot == expected_hot_rows(rows_sorted, I)).all(), "hot rows differ in mode %d" % n
+    b = lay["hot_bit"][n]
+    if b >= 0:
+        got = (keys[:, b // 64] >> np.uint64(b % 64)) & np.uint64(1)
+        ref = np.isin(rows_sorted, hot) if hot.size else np.zeros(len(rows_sorted), bool)
+        assert (got.astype(bool) == ref).all(), "hot flags differ in mode %d" % n
 
 
 @pytest.mark.parametrize("name,nnz", [("uniform3d-64x128x256", None), ("zipf3d-4Mx4Mx30k", 300_000),
