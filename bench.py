@@ -52,6 +52,13 @@ def parse():
     p.add_argument("--variant", type=int, default=0, help="force one MTTKRP variant for every mode")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--nnz", type=int, default=0,
+                   help="profiling only: the workload's generator with fewer nonzeros")
+    p.add_argument("--mttkrp-only", action="store_true",
+                   help="time alto_mttkrp per mode and variant instead of the full step")
+    p.add_argument("--variants", default="0", help="--mttkrp-only: comma-separated variants (0 = auto)")
+    p.add_argument("--modes", default="", help="--mttkrp-only: comma-separated modes (default all)")
+    p.add_argument("--reps", type=int, default=3, help="--mttkrp-only: timed calls per (variant, mode)")
     return p.parse_args()
 
 
@@ -171,15 +178,21 @@ def measured_peak():
 
 
 def kernel_source_hash():
+    """Hash of the MTTKRP kernel sources (a recorded ncu traffic figure is
+    only reported while it matches)."""
+    import glob
     h = hashlib.sha256()
-    for f in ("mttkrp_kernels.cuh", "mttkrp_f32.cu", "mttkrp_bf16.cu", "mttkrp_f64.cu", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2102_10245_gb300", "csrc", f), "rb").read())
+    csrc = os.path.join(ROOT, "paper_2102_10245_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "mttkrp*")) + [os.path.join(csrc, "common.cuh")])
+    for f in files:
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(config, fdtype):
-    """DRAM bytes per MTTKRP launch from a committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def recorded_traffic(config, fdtype, calls):
+    """DRAM bytes per MTTKRP launch (averaged over the timed launches' modes)
+    from a committed ncu summary, if it was taken on the current kernel
+    source (else None)."""
     p = os.path.join(ROOT, "profiles", "mttkrp_dram_traffic.json")
     try:
         d = json.load(open(p))
@@ -188,7 +201,11 @@ def recorded_traffic(config, fdtype):
     e = d.get("%s/%s" % (config, fdtype))
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("bytes_per_launch")
+    per = e.get("bytes_per_launch", {})
+    tot = sum(int(calls[n]) for n in range(len(calls)))
+    if tot == 0 or any(str(n) not in per for n in range(len(calls))):
+        return None
+    return sum(per[str(n)] * int(calls[n]) for n in range(len(calls))) / tot
 
 
 def mttkrp_bytes(nnz, key_bytes, val_bytes, distinct, R, fbytes, obytes, n):
@@ -348,7 +365,7 @@ def run_ours(args, rank, world, local):
     achieved = tot_bytes / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
     peak, peak_src = measured_peak()
     sweep_ms = tot_ms / max(1, int(prof_calls.min()))
-    traffic = recorded_traffic(args.config, fdtype)
+    traffic = recorded_traffic(args.config, fdtype, prof_calls) if not args.nnz else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                 "kernel": "alto MTTKRP (all modes, incl. output zeroing)",
@@ -419,8 +436,46 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_mttkrp_only(args):
+    """Time alto_mttkrp per (variant, mode) on one created tensor; one JSON
+    line per (variant, mode).  Used for kernel profiling."""
+    from paper_2102_10245_gb300 import AltoTensor, torch_allocator
+    import paper_2102_10245_gb300.build as lb
+    lb.build()
+    cfg = synth.scaled(args.config, nnz=args.nnz) if args.nnz else synth.CONFIGS[args.config]
+    fdtype = args.fdtype or cfg["fdtype"]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[fdtype]
+    dims, idx, vals = synth.tensor(cfg)
+    U = synth.factors(cfg)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    idx_d = [torch.from_numpy(a.view(np.int32)).to(dev) for a in idx]
+    vals_d = torch.from_numpy(vals.astype(np.float64 if fdtype == "f64" else np.float32)).to(dev)
+    Ud = [torch.from_numpy(u).to(dev).to(tdt) for u in U]
+    at = AltoTensor(dims, idx_d, vals_d, allocator=torch_allocator())
+    modes = [int(m) for m in args.modes.split(",")] if args.modes else list(range(len(dims)))
+    for v in [int(x) for x in args.variants.split(",")]:
+        for n in modes:
+            at.set_variant(n, v)
+            out = at.mttkrp(n, Ud)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.reps):
+                at.mttkrp(n, Ud, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            print(json.dumps({"workload": args.config, "nnz": len(vals), "dtype": fdtype, "variant": v,
+                              "mode": n, "ms": ms, "gnnz_s": len(vals) / ms / 1e6}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mttkrp_only:
+        torch.cuda.set_device(0)
+        run_mttkrp_only(args)
+        return
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)

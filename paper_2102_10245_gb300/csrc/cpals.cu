@@ -294,6 +294,181 @@ __global__ void __launch_bounds__(kT) normalize_gram_kernel(const typename CT<FT
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-row versions for R in {8, 16, 32, 64}.  W = min(R, 32) lanes hold
+// one row (lane j: columns j + q*W, q < R/W), a warp covers 32/W rows at a
+// time, and row values are broadcast with shuffles inside the row's lanes.
+template <int R>
+struct RowLanes {
+  static constexpr int W = R < 32 ? R : 32;
+  static constexpr int RPW = 32 / W;   // rows per warp pass
+  static constexpr int CPL = R / W;    // columns per lane
+  static constexpr int NB = 4;         // independent passes per iteration (loads in flight)
+};
+
+__device__ __forceinline__ float shfl_w(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_w(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// A = Mt V^{-1} for R in {8,16,32,64}, with the column statistics.
+template <typename C, int R>
+__global__ void __launch_bounds__(kT) solve_rows_kernel(const C* __restrict__ Mt, int64_t I,
+                                                        const C* __restrict__ vinv, C* __restrict__ A,
+                                                        double* __restrict__ colstat, int use_max) {
+  using L = RowLanes<R>;
+  __shared__ C sV[R * R];
+  __shared__ double red[kT / 32][R];
+  for (int e = threadIdx.x; e < R * R; e += kT) sV[e] = vinv[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / L::W, j = lane % L::W;
+  C stat[L::CPL];
+#pragma unroll
+  for (int q = 0; q < L::CPL; ++q) stat[q] = C(0);
+  const int64_t wid = static_cast<int64_t>(blockIdx.x) * (kT / 32) + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kT / 32);
+  constexpr int NB = L::NB;
+  for (int64_t r0 = wid * L::RPW * NB; r0 < I; r0 += nw * L::RPW * NB) {
+    C m[NB][L::CPL], acc[NB][L::CPL];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t row = r0 + b * L::RPW + grp;
+#pragma unroll
+      for (int q = 0; q < L::CPL; ++q) {
+        m[b][q] = row < I ? Mt[row * R + j + q * L::W] : C(0);
+        acc[b][q] = C(0);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      C v[L::CPL];
+#pragma unroll
+      for (int q = 0; q < L::CPL; ++q) v[q] = sV[k * R + j + q * L::W];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const C mk = shfl_w(m[b][k / L::W], grp * L::W + (k % L::W));
+#pragma unroll
+        for (int q = 0; q < L::CPL; ++q) acc[b][q] = fma(mk, v[q], acc[b][q]);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t row = r0 + b * L::RPW + grp;
+      if (row < I) {
+#pragma unroll
+        for (int q = 0; q < L::CPL; ++q) {
+          A[row * R + j + q * L::W] = acc[b][q];
+          stat[q] = use_max ? fmax(stat[q], fabs(acc[b][q])) : fma(acc[b][q], acc[b][q], stat[q]);
+        }
+      }
+    }
+  }
+  // column statistics: combine the row groups of the warp, then the warps
+#pragma unroll
+  for (int q = 0; q < L::CPL; ++q) {
+    double v = static_cast<double>(stat[q]);
+    for (int o = L::W; o < 32; o <<= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, v, o);
+      v = use_max ? fmax(v, y) : v + y;
+    }
+    if (grp == 0) red[warp][j + q * L::W] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < R; c += kT) {
+    double v = 0.0;
+    for (int w = 0; w < kT / 32; ++w) v = use_max ? fmax(v, red[w][c]) : v + red[w][c];
+    if (use_max)
+      atomic_max_nonneg(colstat + c, v);
+    else
+      atomicAdd(colstat + c, v);
+  }
+}
+
+// U = A / lambda (stored as FT), G += U^T U, and optionally
+// ip += sum_r lambda_r sum_i U[i,r] Mt[i,r].  A warp owns one column block of
+// the Gram (columns cb*W + j; R/W blocks), accumulates G[:, its columns] over
+// its rows in registers (FP32 partials for FP32/BF16 storage), and the
+// partials are summed in FP64 through shared memory, then into G.
+template <typename FT, int R>
+__global__ void __launch_bounds__(kT) normalize_gram_rows_kernel(
+    const typename CT<FT>::type* __restrict__ A, int64_t I, const double* __restrict__ colstat, int use_max,
+    double* __restrict__ lambda, FT* __restrict__ U, double* __restrict__ G,
+    const typename CT<FT>::type* __restrict__ Mt, double* __restrict__ ip) {
+  using C = typename CT<FT>::type;
+  using L = RowLanes<R>;
+  constexpr int NCB = L::CPL;  // column blocks of the Gram
+  __shared__ C inv[R];
+  __shared__ double lam[R];
+  __shared__ double gred[R * R];
+  __shared__ double ipred[kT / 32];
+  for (int r = threadIdx.x; r < R; r += kT) {
+    const double l = use_max ? fmax(colstat[r], 1.0) : sqrt(colstat[r]);
+    lam[r] = l;
+    inv[r] = static_cast<C>(1.0 / l);
+    if (blockIdx.x == 0) lambda[r] = l;
+  }
+  for (int e = threadIdx.x; e < R * R; e += kT) gred[e] = 0.0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / L::W, j = lane % L::W;
+  const int cb = warp % NCB;
+  C g[R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) g[a] = C(0);
+  double ipd = 0.0;
+  const int64_t wid = static_cast<int64_t>(blockIdx.x) * (kT / 32 / NCB) + warp / NCB;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kT / 32 / NCB);
+  constexpr int NB = L::NB;
+  for (int64_t r0 = wid * L::RPW * NB; r0 < I; r0 += nw * L::RPW * NB) {
+    C u[NB][L::CPL];
+    C own[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t row = r0 + b * L::RPW + grp;
+      const bool ok = row < I;
+#pragma unroll
+      for (int q = 0; q < L::CPL; ++q) {
+        const int col = j + q * L::W;
+        u[b][q] = C(0);
+        if (ok) {
+          const FT st = static_cast<FT>(A[row * R + col] * inv[col]);
+          u[b][q] = to_ct<FT>(st);
+          if (q == cb) {  // the warp of column block q stores it
+            U[row * R + col] = st;
+            if (Mt != nullptr) ipd += static_cast<double>(u[b][q] * Mt[row * R + col]) * lam[col];
+          }
+        }
+      }
+      own[b] = u[b][0];
+#pragma unroll
+      for (int q = 1; q < L::CPL; ++q)
+        if (q == cb) own[b] = u[b][q];
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const C ua = shfl_w(u[b][a / L::W], grp * L::W + (a % L::W));
+        g[a] = fma(ua, own[b], g[a]);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    double v = static_cast<double>(g[a]);
+    for (int o = L::W; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (grp == 0) atomicAdd(&gred[a * R + cb * L::W + j], v);
+  }
+  for (int o = 16; o > 0; o >>= 1) ipd += __shfl_xor_sync(0xffffffffu, ipd, o);
+  if (lane == 0) ipred[warp] = ipd;
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += kT) atomicAdd(G + e, gred[e]);
+  if (Mt != nullptr && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += ipred[w];
+    atomicAdd(ip, t);
+  }
+}
+
 // fit = 1 - sqrt(max(0, ||X||^2 + lambda^T (Hadamard G) lambda - 2 ip)) / ||X||
 __global__ void __launch_bounds__(kT) fit_kernel(const double* __restrict__ G, int N, int R,
                                                  const double* __restrict__ lambda, double normX2,
@@ -379,17 +554,39 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
       const C* vinv = std::is_same<C, double>::value ? reinterpret_cast<const C*>(w.vinv64)
                                                       : reinterpret_cast<const C*>(w.vinv32);
       if (In > 0) {
-        solve_kernel<C><<<rows_grid(In, kT / R, 8), kT, 0, s>>>(static_cast<const C*>(w.mt), In, R, vinv,
-                                                               static_cast<C*>(w.atmp), w.colstat, use_max);
+        const C* mt = static_cast<const C*>(w.mt);
+        C* at = static_cast<C*>(w.atmp);
+        const unsigned gr = rows_grid(In, 32 * 8, 8);
+        switch (R) {
+          case 8: solve_rows_kernel<C, 8><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 16: solve_rows_kernel<C, 16><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 32: solve_rows_kernel<C, 32><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 64: solve_rows_kernel<C, 64><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          default:
+            solve_kernel<C><<<rows_grid(In, kT / R, 8), kT, 0, s>>>(mt, In, R, vinv, at, w.colstat, use_max);
+        }
         note_launch();
         CK(cudaGetLastError());
       }
       CK(cudaMemsetAsync(w.gram + n * RR, 0, sizeof(double) * RR, s));
       const bool last = (n == N - 1);
       if (last) CK(cudaMemsetAsync(w.scal, 0, sizeof(double), s));
-      normalize_gram_kernel<FT><<<rows_grid(In, kGramRows, 4), kT, 0, s>>>(
-          static_cast<const C*>(w.atmp), In, R, w.colstat, use_max, lambda, static_cast<FT*>(factors[n]),
-          w.gram + n * RR, last ? static_cast<const C*>(w.mt) : nullptr, w.scal);
+      {
+        const C* at = static_cast<const C*>(w.atmp);
+        FT* un = static_cast<FT*>(factors[n]);
+        double* gn = w.gram + n * RR;
+        const C* mt = last ? static_cast<const C*>(w.mt) : nullptr;
+        const unsigned gr = rows_grid(In, 32 * 8, 8);
+        switch (R) {
+          case 8: normalize_gram_rows_kernel<FT, 8><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          case 16: normalize_gram_rows_kernel<FT, 16><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          case 32: normalize_gram_rows_kernel<FT, 32><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          case 64: normalize_gram_rows_kernel<FT, 64><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          default:
+            normalize_gram_kernel<FT><<<rows_grid(In, kGramRows, 4), kT, 0, s>>>(at, In, R, w.colstat, use_max, lambda, un,
+                                                                               gn, mt, w.scal);
+        }
+      }
       note_launch();
       CK(cudaGetLastError());
     }

@@ -18,29 +18,47 @@ struct EncodeParams {
   int nmodes;
   uint64_t dims[kMaxModes];
   int nbits[kMaxModes];
-  uint8_t pos[kMaxModes][32];
 };
 
+// Bit-level deposit of every mode index into its key positions: per 32-bit
+// key word, the slice of the index that the word holds is spread over the
+// word's mask with the five-step parallel-suffix "expand" (Hacker's Delight,
+// 2nd ed., Sec. 7-5), the inverse of the compress the kernels use to
+// de-linearize, driven by the same move masks.
 template <typename IT, int KW>
-__global__ void __launch_bounds__(256) encode_kernel(const __grid_constant__ EncodeParams ep,
+__global__ void __launch_bounds__(256) encode_kernel(const __grid_constant__ DecodeParams dp,
+                                                     const __grid_constant__ EncodeParams ep,
                                                      const __grid_constant__ IdxPtrs idx, int64_t M,
                                                      uint64_t* __restrict__ keys, int* status) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride) {
-    uint64_t w[2] = {0, 0};
-    for (int n = 0; n < ep.nmodes; ++n) {
+    uint32_t w[2 * KW];
+#pragma unroll
+    for (int q = 0; q < 2 * KW; ++q) w[q] = 0;
+    for (int n = 0; n < dp.nmodes; ++n) {
       uint64_t i = static_cast<uint64_t>(__ldcs(static_cast<const IT*>(idx.p[n]) + x));
       if (i >= ep.dims[n]) {
         set_status(status, ALTO_ERANGE);
         i = 0;
       }
-      for (int l = 0; l < ep.nbits[n]; ++l) {
-        const int p = ep.pos[n][l];
-        w[p >> 6] |= ((i >> l) & 1ull) << (p & 63);
+      const uint32_t i32 = static_cast<uint32_t>(i);
+#pragma unroll
+      for (int q = 0; q < 2 * KW; ++q) {
+        const uint32_t m = dp.mask[n][q];
+        if (m != 0u) {
+          uint32_t v = dp.shift[n][q] < 32 ? (i32 >> dp.shift[n][q]) : 0u;
+#pragma unroll
+          for (int k = 4; k >= 0; --k) {
+            const uint32_t mv = dp.mv[n][q][k];
+            v = (v & ~mv) | ((v << (1u << k)) & mv);
+          }
+          w[q] |= v & m;
+        }
       }
     }
-    keys[x * KW] = w[0];
-    if (KW == 2) keys[x * KW + 1] = w[1];
+#pragma unroll
+    for (int q = 0; q < KW; ++q)
+      keys[x * KW + q] = static_cast<uint64_t>(w[2 * q]) | (static_cast<uint64_t>(w[2 * q + 1]) << 32);
   }
 }
 
@@ -87,10 +105,12 @@ struct RowArrays {
   uint32_t* cnt[kMaxModes];  // sampled nonzeros per row (every kHotSample-th)
 };
 
-// One warp per segment.  Lanes walk the segment, decode every mode, keep
-// running min/max, and record the lowest / highest segment that touches
-// each row (atomicMin / atomicMax; a lane skips the atomic when its
-// previous element had the same row).
+// One warp per segment.  Lanes walk the segment 32 elements at a time,
+// decode every mode, keep running min/max, and record the lowest / highest
+// segment that touches each row and the sampled row counts.  Lanes holding
+// the same row are matched first so that one lane per row issues the
+// atomics, and a first/last value already at least as good is not touched:
+// the heavy rows of skewed tensors would otherwise serialise on one address.
 template <int KW>
 __global__ void __launch_bounds__(256) segment_stats_kernel(const __grid_constant__ DecodeParams dp,
                                                             const uint64_t* __restrict__ keys,
@@ -110,20 +130,32 @@ __global__ void __launch_bounds__(256) segment_stats_kernel(const __grid_constan
       hi[n] = 0;
       prev[n] = 0xffffffffu;
     }
-    for (int64_t x = s0 + lane; x < s1; x += 32) {
-      const KeyT<KW> k = load_key<KW>(keys, x);
+    const uint32_t useg = static_cast<uint32_t>(seg);
+    for (int64_t base = s0; base < s1; base += 32) {
+      const int64_t x = base + lane;
+      const bool ok = x < s1;
+      KeyT<KW> k{};
+      if (ok) k = load_key<KW>(keys, x);
+      const uint32_t sampled = __ballot_sync(0xffffffffu, ok && (x % kHotSample) == 0);
 #pragma unroll
       for (int n = 0; n < kMaxModes; ++n) {
         if (n < N) {
           const uint32_t i = extract<KW>(k, dp, n);
-          lo[n] = min(lo[n], i);
-          hi[n] = max(hi[n], i);
-          if (i != prev[n]) {
-            atomicMin(ra.first[n] + i, static_cast<uint32_t>(seg));
-            if (ra.last[n] != nullptr) atomicMax(ra.last[n] + i, static_cast<uint32_t>(seg));
-            prev[n] = i;
+          if (ok) {
+            lo[n] = min(lo[n], i);
+            hi[n] = max(hi[n], i);
           }
-          if (ra.cnt[n] != nullptr && (x % kHotSample) == 0) atomicAdd(ra.cnt[n] + i, 1u);
+          const unsigned long long tag = ok ? static_cast<unsigned long long>(i) : (0x100000000ull + lane);
+          const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+          if (ok && lane == __ffs(peers) - 1 && i != prev[n]) {
+            if (ra.first[n][i] > useg) atomicMin(ra.first[n] + i, useg);
+            if (ra.last[n] != nullptr && ra.last[n][i] < useg) atomicMax(ra.last[n] + i, useg);
+          }
+          if (ok && lane == __ffs(peers) - 1) {
+            prev[n] = i;
+            const uint32_t ns = __popc(peers & sampled);
+            if (ra.cnt[n] != nullptr && ns) atomicAdd(ra.cnt[n] + i, ns);
+          }
         }
       }
     }
@@ -251,19 +283,22 @@ cudaError_t launch_encode(const Layout& lay, const IdxPtrs& idx, int idx_bytes, 
   for (int n = 0; n < lay.N; ++n) {
     ep.dims[n] = lay.dims[n];
     ep.nbits[n] = lay.nbits[n];
-    for (int l = 0; l < lay.nbits[n]; ++l) ep.pos[n][l] = static_cast<uint8_t>(lay.pos[n][l]);
   }
+  DecodeParams dp;
+  int ident[kMaxModes];
+  for (int n = 0; n < kMaxModes; ++n) ident[n] = n;
+  make_decode(lay, ident, &dp);
   const unsigned g = grid_for(M, 256);
   if (idx_bytes == 4) {
     if (lay.KW == 1)
-      encode_kernel<uint32_t, 1><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+      encode_kernel<uint32_t, 1><<<g, 256, 0, s>>>(dp, ep, idx, M, keys, status);
     else
-      encode_kernel<uint32_t, 2><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+      encode_kernel<uint32_t, 2><<<g, 256, 0, s>>>(dp, ep, idx, M, keys, status);
   } else {
     if (lay.KW == 1)
-      encode_kernel<int64_t, 1><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+      encode_kernel<int64_t, 1><<<g, 256, 0, s>>>(dp, ep, idx, M, keys, status);
     else
-      encode_kernel<int64_t, 2><<<g, 256, 0, s>>>(ep, idx, M, keys, status);
+      encode_kernel<int64_t, 2><<<g, 256, 0, s>>>(dp, ep, idx, M, keys, status);
   }
   note_launch();
   return cudaGetLastError();

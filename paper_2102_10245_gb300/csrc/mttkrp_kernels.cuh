@@ -334,7 +334,7 @@ __device__ __forceinline__ void flush_shared(typename FTraits<FT>::AT* rowp, int
 // ---------------------------------------------------------------------------
 // The kernel.
 template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+__global__ void __launch_bounds__(kThreads, 5) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   using C = Cols<R, FT>;

@@ -9,8 +9,9 @@
 //                         first output slot;
 //   3. scatter         -- each tile ranks its keys stably (warp match on the
 //                         digit inside 32-key rounds, running per-warp digit
-//                         counts, then a prefix over the tile's warps) and
-//                         writes keys and positions to their slots.
+//                         counts, then a prefix over the tile's warps),
+//                         stages them in shared memory in digit order and
+//                         writes every digit's run out contiguously.
 // Equal keys keep their input order (LSD passes are each stable), which is
 // what the ordering stage needs when duplicates are present.  The passes
 // never wait on one another inside a kernel, so no device spin is needed.
@@ -72,6 +73,11 @@ __global__ void __launch_bounds__(kSortThreads) tile_scatter(
     uint64_t* __restrict__ keys_out, uint32_t* __restrict__ perm_out, int64_t M, int shift,
     int64_t ntiles, const uint32_t* __restrict__ offsets, int iota_perm) {
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t tstart[kRadix];   // first staged slot of each digit
+  __shared__ uint32_t gbase[kRadix];    // first output slot of each digit for this tile
+  extern __shared__ __align__(16) unsigned char stage_raw[];
+  uint64_t* skey = reinterpret_cast<uint64_t*>(stage_raw);             // kTile x KW
+  uint32_t* sperm = reinterpret_cast<uint32_t*>(skey + kTile * KW);   // kTile
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
@@ -109,7 +115,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_scatter(
     local[r] = base + __popc(peers & lt);
   }
   __syncthreads();
-  // exclusive prefix over the tile's warps, per digit (in place)
+  // exclusive prefix over the tile's warps, per digit (in place); digit totals
   for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
     uint32_t s = 0;
 #pragma unroll
@@ -118,19 +124,57 @@ __global__ void __launch_bounds__(kSortThreads) tile_scatter(
       wcnt[w][d] = s;
       s += c;
     }
+    tstart[d] = s;  // total of digit d (turned into a start below)
+    gbase[d] = offsets[static_cast<int64_t>(d) * ntiles + tile];
   }
   __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+    uint32_t v[kRadix / 32];
+    uint32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < kRadix / 32; ++q) {
+      v[q] = tstart[threadIdx.x * (kRadix / 32) + q];
+      run += v[q];
+    }
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (threadIdx.x >= o) inc += y;
+    }
+    uint32_t base = inc - run;
+#pragma unroll
+    for (int q = 0; q < kRadix / 32; ++q) {
+      tstart[threadIdx.x * (kRadix / 32) + q] = base;
+      base += v[q];
+    }
+  }
+  __syncthreads();
+  // stage in digit order
 #pragma unroll
   for (int r = 0; r < kItems; ++r) {
     const int64_t x = wbase + r * 32 + lane;
     if (x < M) {
       const uint32_t d = dg[r];
-      const int64_t dst = static_cast<int64_t>(offsets[static_cast<int64_t>(d) * ntiles + tile]) +
-                          wcnt[warp][d] + local[r];
+      const uint32_t pos = tstart[d] + wcnt[warp][d] + local[r];
 #pragma unroll
-      for (int w = 0; w < KW; ++w) keys_out[dst * KW + w] = k[r][w];
-      perm_out[dst] = pv[r];
+      for (int w = 0; w < KW; ++w) skey[pos * KW + w] = k[r][w];
+      sperm[pos] = pv[r];
     }
+  }
+  __syncthreads();
+  // write out: consecutive staged slots of one digit go to consecutive slots
+  const int64_t tbase = tile * kTile;
+  const int n = static_cast<int>(M - tbase < kTile ? M - tbase : kTile);
+  for (int i = threadIdx.x; i < n; i += kSortThreads) {
+    uint64_t kk[KW];
+#pragma unroll
+    for (int w = 0; w < KW; ++w) kk[w] = skey[i * KW + w];
+    const uint32_t d = digit_of<KW>(kk, shift);
+    const int64_t dst = static_cast<int64_t>(gbase[d]) + (i - tstart[d]);
+#pragma unroll
+    for (int w = 0; w < KW; ++w) keys_out[dst * KW + w] = kk[w];
+    perm_out[dst] = sperm[i];
   }
 }
 
@@ -252,11 +296,14 @@ cudaError_t radix_sort_pairs(uint64_t** keys, uint64_t** keys_alt, uint32_t** pe
     }
     cudaError_t e = exclusive_scan_u32(counts, offsets, ncount, part, s);
     if (e != cudaSuccess) return e;
+    const size_t stage = static_cast<size_t>(kTile) * (8 * KW + 4);
     if (KW == 1) {
-      tile_scatter<1><<<static_cast<unsigned>(ntiles), kSortThreads, 0, s>>>(
+      if (p == 0) cudaFuncSetAttribute(tile_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(stage));
+      tile_scatter<1><<<static_cast<unsigned>(ntiles), kSortThreads, stage, s>>>(
           *keys, *perm, *keys_alt, *perm_alt, M, shift, ntiles, offsets, iota ? 1 : 0);
     } else {
-      tile_scatter<2><<<static_cast<unsigned>(ntiles), kSortThreads, 0, s>>>(
+      if (p == 0) cudaFuncSetAttribute(tile_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(stage));
+      tile_scatter<2><<<static_cast<unsigned>(ntiles), kSortThreads, stage, s>>>(
           *keys, *perm, *keys_alt, *perm_alt, M, shift, ntiles, offsets, iota ? 1 : 0);
     }
     note_launch(2);
