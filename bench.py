@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--variants", default="0", help="--mttkrp-only: comma-separated variants (0 = auto)")
     p.add_argument("--modes", default="", help="--mttkrp-only: comma-separated modes (default all)")
     p.add_argument("--reps", type=int, default=3, help="--mttkrp-only: timed calls per (variant, mode)")
+    p.add_argument("--batch-items", type=int, default=256, help="batched workload: held-out tensors")
+    p.add_argument("--train-items", type=int, default=2000, help="batched workload: training tensors")
+    p.add_argument("--err-items", type=int, default=8, help="batched workload: tensors checked against FP64")
     return p.parse_args()
 
 
@@ -436,6 +439,195 @@ def run_ours(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+BATCH_CONFIG = "batched-256"
+BATCH_HELDOUT = 100_000          # seeds of the held-out batched tensors
+TIMINGS = os.path.join(ROOT, "paper_2102_10245_gb300", "data", "variant_timings.npz")
+
+
+def _time_k(fn, k, stream):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def run_batched(args, rank, world, local):
+    """The batched + learned workload: all-mode MTTKRP of 256 seeded tensors
+    of order 3-5 (nnz 10k-5M, lengths 100-10M, uniform / Zipf / clustered,
+    R in {8, 16, 32, 64}).  Headline: BF16 factors, every (tensor, mode) in
+    one graph-captured batch, variants picked by the MLP trained on the
+    autotuner timings of 2,000 other seeded tensors.  Beside it: the plain
+    FP32 form (one alto_mttkrp call per tensor and mode, built-in rule) and
+    the predictor's regret against the autotuned picks of these tensors."""
+    from paper_2102_10245_gb300 import AltoTensor, Batch, launch_count
+    from paper_2102_10245_gb300 import autotune as tune
+    import paper_2102_10245_gb300.build as lb
+    lb.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    K, W = args.steps, max(args.warmup, 0)
+    log = lambda m: print("[batched %.0fs] %s" % (time.time() - t_start, m), file=sys.stderr, flush=True)  # noqa
+    t_start = time.time()
+
+    seeds = list(range(BATCH_HELDOUT, BATCH_HELDOUT + args.batch_items))
+    cfgs = [synth.batch_config(s) for s in seeds]
+    tensors = []
+    for cfg in cfgs:
+        dims, idx, vals = synth.tensor_torch(cfg, dev)
+        tensors.append(AltoTensor(dims, idx, vals))
+        del idx, vals
+    work = sum(at.nnz * at.N for at in tensors)
+    log("created %d tensors, %.1f M nonzeros" % (len(tensors), sum(at.nnz for at in tensors) / 1e6))
+
+    # plain FP32: one call per (tensor, mode), the built-in variant rule
+    f32 = [synth.factors_torch(cfg, dev, torch.float32) for cfg in cfgs]
+    outs = [[torch.empty(d, cfg["rank"], dtype=torch.float32, device=dev) for d in cfg["dims"]] for cfg in cfgs]
+
+    def plain():
+        for at, U, O in zip(tensors, f32, outs):
+            for n in range(at.N):
+                at.mttkrp(n, U, out=O[n])
+    for _ in range(W):
+        plain()
+    torch.cuda.synchronize()
+    ms_plain = _time_k(plain, K, stream)
+    items32 = [(at, n, U, O[n]) for at, U, O in zip(tensors, f32, outs) for n in range(at.N)]
+    b32 = Batch(items32)
+    for _ in range(W):
+        b32.run()
+    ms_b32_rule = _time_k(b32.run, K, stream)
+    b32.close()
+    del b32, items32
+    log("plain FP32 %.2f ms, FP32 batched (rule) %.2f ms" % (ms_plain, ms_b32_rule))
+
+    # BF16 factors (the same values rounded), FP32 copies released one by one
+    bf = []
+    for U in f32:
+        bf.append([u.to(torch.bfloat16) for u in U])
+        U.clear()
+    del f32
+    torch.cuda.empty_cache()
+    items = [(at, n, U, O[n]) for at, U, O in zip(tensors, bf, outs) for n in range(at.N)]
+    feats = np.array([tune.features(at, n, U[0].shape[1]) for at, n, U, _ in items])
+    rule = np.array([tune.rule_pick(at, n, U[0].shape[1]) for at, n, U, _ in items])
+
+    # the predictor: trained on the GPU by libalto's nn kernels
+    if os.path.exists(TIMINGS):
+        d = np.load(TIMINGS)
+        tr_f, tr_t, src = d["train_features"], d["train_times"], os.path.relpath(TIMINGS, ROOT)
+    else:
+        log("no stored timings: collecting the training set now")
+        d = tune.collect(range(0, args.train_items), log=log)
+        tr_f, tr_t, src = d["features"], d["times"], "collected in this run"
+    pred = tune.Predictor(seed=0)
+    t0 = time.perf_counter()
+    losses = pred.fit(tr_f, tr_t)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    picks = pred.pick(feats)
+    infer_ms = (time.perf_counter() - t0) * 1e3
+    log("predictor trained in %.1f s (loss %.4f -> %.4f)" % (train_s, losses[0], losses[-1]))
+
+    # the autotuner on the held-out items: the judge of the predictor
+    times = np.array([tune.time_variants(at, n, U, O) for at, n, U, O in items])
+    best = times.argmin(axis=1)
+    reg_mlp = tune.regret(times, picks)
+    reg_rule = tune.regret(times, rule)
+    log("regret: predictor %.3f / %.3f, rule %.3f / %.3f" % (reg_mlp + reg_rule))
+
+    def batch_ms(sel):
+        b = Batch(items, variants=[tune.VARIANTS[p] for p in sel])
+        for _ in range(W):
+            b.run()
+        ms = _time_k(b.run, K, stream)
+        info = b.info()
+        b.close()
+        return ms, info
+    ms_rule, _ = batch_ms(rule)
+    ms_best, _ = batch_ms(best)
+    bh = Batch(items, variants=[tune.VARIANTS[p] for p in picks])
+    for _ in range(W):
+        bh.run()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = launch_count()
+    ms = _time_k(bh.run, K, stream)
+    launches = launch_count() - n0
+    clk = clocks.stop()
+    info = bh.info()
+
+    # error of the BF16 batch against FP64 on the smallest tensors
+    import oracle
+    errs = []
+    small = sorted(range(len(tensors)), key=lambda i: tensors[i].nnz)[:args.err_items]
+    bh.run()
+    torch.cuda.synchronize()
+    for i in small:
+        cfg = cfgs[i]
+        dims, idx, vals = synth.tensor_torch(cfg, dev)
+        idx_h = [a.cpu().numpy().view(np.uint32) for a in idx]
+        vals_h = vals.cpu().numpy().astype(np.float64)
+        U64 = [u.cpu().numpy().astype(np.float64) for u in synth.factors_torch(cfg, dev, torch.float32)]
+        for n in range(len(dims)):
+            ref = oracle.mttkrp(dims, idx_h, vals_h, U64, n)
+            got = outs[i][n].cpu().numpy().astype(np.float64)
+            errs.append(float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)))
+    bh.close()
+
+    # roofline of the batch: compulsory bytes of every item over the graph time
+    tot_bytes = 0
+    for at, n, U, _ in items:
+        st = at.stats()
+        kb = 8 * at.layout()["key_words"]
+        tot_bytes += mttkrp_bytes(at.nnz, kb, 4, st["distinct"], U[0].shape[1], 2, 4, n)
+    peak, peak_src = measured_peak()
+    achieved = tot_bytes / (ms / 1e3) / 1e9
+    value = work / (ms / 1e3) / 1e9
+    if rank != 0:
+        return
+    lab = tune.VARIANT_LABELS
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "%s: all-mode MTTKRP of %d seeded tensors (order 3-5, nnz 10k-5M log-uniform, "
+                               "lengths 100-10M, uniform/Zipf/clustered, R in {8,16,32,64})"
+                               % (BATCH_CONFIG, len(tensors)),
+                   "nnz_total": int(sum(at.nnz for at in tensors)), "items": len(items),
+                   "step": "one graph replay: every (tensor, mode) MTTKRP, BF16 factors, FP32 accumulation",
+                   "l2": "inputs larger than L2 (%.1f GB of keys and values)"
+                         % (sum(at.nnz for at in tensors) * 12 / 1e9)},
+        "plain_fp32": {"ms": ms_plain, "gnnz_s": work / (ms_plain / 1e3) / 1e9,
+                       "form": "one alto_mttkrp call per (tensor, mode), FP32 factors, built-in variant rule"},
+        "speedup_vs_plain_fp32": ms_plain / ms,
+        "context": {"fp32_batched_rule_ms": ms_b32_rule, "bf16_batched_rule_ms": ms_rule,
+                    "bf16_batched_autotuned_ms": ms_best},
+        "predictor": {"train": src, "train_rows": int(len(tr_f)), "train_s": train_s, "infer_ms": infer_ms,
+                      "loss_first_last": [losses[0], losses[-1]],
+                      "regret_total": reg_mlp[0], "regret_mean": reg_mlp[1],
+                      "rule_regret_total": reg_rule[0], "rule_regret_mean": reg_rule[1],
+                      "picks": {lab[v]: int((picks == v).sum()) for v in range(len(lab))},
+                      "autotuned": {lab[v]: int((best == v).sum()) for v in range(len(lab))}},
+        "rel_err_vs_fp64": {"max": max(errs) if errs else None, "items": len(errs),
+                            "sample": "every mode of the %d smallest tensors" % len(small)},
+        "batch": info,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": peak_src,
+                     "kernel": "the whole batch graph (group kernels, hot-row reduce, output zeroing)"},
+        "cpu_baseline": None,
+        "e2e": None,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_mttkrp_only(args):
     """Time alto_mttkrp per (variant, mode) on one created tensor; one JSON
     line per (variant, mode).  Used for kernel profiling."""
@@ -479,6 +671,8 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == BATCH_CONFIG:
+        run_batched(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -30,6 +30,7 @@ extern "C" {
 #endif
 
 typedef struct alto_tensor_s *alto_t;
+typedef struct alto_batch_s *alto_batch_t;
 
 typedef enum {
     ALTO_OK = 0,
@@ -209,8 +210,58 @@ alto_status alto_get_stats(alto_t t, int64_t *nnz, int64_t *nparts,
 alto_status alto_export(alto_t t, uint64_t *keys, uint32_t *perm, void *vals,
                         int64_t *bounds, uint32_t *intervals);
 
+/*
+ * alto_get_mode_stats -- statistics of one mode, for variant selection.
+ * out[0..n) (n <= 8 used): 0 length I_n, 1 distinct rows D_n, 2 reuse M/I_n,
+ * 3 widest segment interval, 4 hot rows, 5 share of the sampled nonzeros
+ * that fall in the hot rows, 6 median and 7 90th-percentile width of the
+ * thread-block units' intervals (8 consecutive segments).
+ */
+alto_status alto_get_mode_stats(alto_t t, int mode, double *out, int n);
+
+/* alto_get_unit_fit -- fraction of thread-block units whose mode-`mode`
+ * interval has at most `rows` rows (how often a shared Temp of that many rows
+ * holds a unit's output). */
+alto_status alto_get_unit_fit(alto_t t, int mode, uint64_t rows, double *frac);
+
+/*
+ * Kernels of the variant-predictor MLP (row-major FP32, device pointers,
+ * asynchronous on `stream`).  The paper has no counterpart: the predictor
+ * picks the MTTKRP variant from tensor statistics.
+ *   alto_nn_linear_forward : Y[n x dout] = act(X[n x din] W^T + b), W is
+ *                            dout x din, act = ReLU when relu != 0.
+ *   alto_nn_linear_backward: G = dY * act'(Y) (written to G, n x dout);
+ *                            dW = G^T X, db = sum_rows G, dX = G W (dX may be
+ *                            NULL).
+ *   alto_nn_mse            : loss (device double) = sum(mask (P-T)^2) / norm,
+ *                            dP = 2 mask (P-T) / norm; mask may be NULL.
+ *   alto_nn_adam           : one Adam step (bias-corrected, step >= 1).
+ */
+alto_status alto_nn_linear_forward(const float *X, const float *W,
+                                   const float *b, float *Y, int n, int din,
+                                   int dout, int relu, void *stream);
+alto_status alto_nn_linear_backward(const float *X, const float *W,
+                                    const float *Y, const float *dY, float *G,
+                                    float *dX, float *dW, float *db, int n,
+                                    int din, int dout, int relu, void *stream);
+alto_status alto_nn_mse(const float *P, const float *T, const float *mask,
+                        float *dP, int64_t count, double norm, double *loss,
+                        void *stream);
+alto_status alto_nn_adam(float *param, const float *grad, float *m, float *v,
+                         int64_t count, float lr, float beta1, float beta2,
+                         float eps, int step, void *stream);
+
 /* alto_set_variant -- override the MTTKRP variant of one mode. */
 alto_status alto_set_variant(alto_t t, int mode, int variant);
+
+/* alto_resolve_variant -- the accumulation variant an alto_mttkrp call of
+ * this mode, rank and factor dtype runs when it asks for `variant`
+ * (ALTO_VAR_AUTO: the per-mode override, else the reuse rule of Sec. 3.3
+ * adapted to the GPU: reuse M/I_n <= 4 -> ATOMIC; else SMEM when 9 in 10
+ * thread-block units' output intervals fit the shared buffer; else
+ * WARPAGG).  Shapes without a specialised kernel report ATOMIC (the generic
+ * kernel).  *out receives one of ALTO_VAR_ATOMIC..ALTO_VAR_TEMP.  Host-only. */
+alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_dtype fdtype, int variant, int *out);
 
 /* alto_check -- synchronise `stream` and report a recorded device error. */
 alto_status alto_check(alto_t t, void *stream);
@@ -284,6 +335,39 @@ alto_status alto_linearize_noalloc(int nmodes, const uint64_t *dims,
                                    int64_t nnz, const void *const *idx,
                                    int idx_bytes, uint64_t *keys,
                                    uint32_t *perm, void *stream);
+
+/*
+ * alto_batch_create -- plan many MTTKRPs (all modes of many tensors, of
+ * uneven order and size) as one CUDA graph.  Item i is the mode-modes[i]
+ * MTTKRP of tensors[i] with factors[i] (host array of that tensor's N device
+ * pointers), rank ranks[i], factor dtype fdtype (shared by all items) and
+ * output outs[i] (as for alto_mttkrp), using variants[i] (alto_variant, 0 =
+ * automatic; NULL = all automatic).  Items of one kernel shape (order, key
+ * width, rank, variant) run in one persistent launch over a device work list
+ * of their thread-block units; items without a specialised kernel run on
+ * their own; the device-memory Temp variant is replaced by warp aggregation.
+ * The graph captures the given pointers: later runs read the factors' and
+ * write the outputs' current contents.  Capture happens on `stream` (on a
+ * private stream when `stream` is the legacy default stream, which cannot
+ * be captured); the plan owns its device buffers.
+ */
+alto_status alto_batch_create(alto_batch_t *out, int count,
+                              const alto_t *tensors, const int *modes,
+                              const void *const *const *factors,
+                              const int *ranks, alto_dtype fdtype,
+                              void *const *outs, const int *variants,
+                              void *stream);
+
+/* alto_batch_run -- launch the plan's graph on `stream` (asynchronous). */
+alto_status alto_batch_run(alto_batch_t b, void *stream);
+
+/* alto_batch_info -- items, persistent group launches, stand-alone items,
+ * and kernel launches per alto_batch_run (any pointer may be NULL). */
+alto_status alto_batch_info(alto_batch_t b, int *items, int *groups,
+                            int *single, int *kernels);
+
+/* alto_batch_destroy -- free the plan.  NULL is accepted. */
+alto_status alto_batch_destroy(alto_batch_t b);
 
 /* alto_destroy -- free everything the handle owns.  NULL is accepted. */
 alto_status alto_destroy(alto_t t);

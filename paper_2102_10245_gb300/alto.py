@@ -59,6 +59,7 @@ def lib():
             "alto_get_stats": [P, P, P, P, P, P, P],
             "alto_export": [P, P, P, P, P, P],
             "alto_set_variant": [P, I, I],
+            "alto_resolve_variant": [P, I, I, I, I, P],
             "alto_check": [P, P],
             "alto_destroy": [P],
             "alto_layout_for_dims": [I, P, I, P, P, P, P],
@@ -67,6 +68,16 @@ def lib():
             "alto_profile_read": [P, P, P],
             "alto_launch_count": [P],
             "alto_linearize_noalloc": [I, P, I64, P, I, P, P, P],
+            "alto_batch_create": [P, I, P, P, P, P, I, P, P, P],
+            "alto_batch_run": [P, P],
+            "alto_batch_info": [P, P, P, P, P],
+            "alto_batch_destroy": [P],
+            "alto_get_mode_stats": [P, I, P, I],
+            "alto_get_unit_fit": [P, I, ctypes.c_uint64, P],
+            "alto_nn_linear_forward": [P, P, P, P, I, I, I, I, P],
+            "alto_nn_linear_backward": [P, P, P, P, P, P, P, P, I, I, I, I, P],
+            "alto_nn_mse": [P, P, P, P, I64, ctypes.c_double, P, P],
+            "alto_nn_adam": [P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -153,6 +164,62 @@ def torch_allocator():
             live.pop(ptr, None)
             torch.cuda.caching_allocator_delete(ptr)
     return _alloc, _free
+
+
+class Batch:
+    """Many MTTKRPs captured as one CUDA graph (alto_batch_create).
+
+    items: list of (AltoTensor, mode, factors (list of device tensors),
+    out (device tensor)); all factors share one dtype.  variants: optional
+    per-item variant list."""
+
+    def __init__(self, items, variants=None, stream=None):
+        n = len(items)
+        self._items = items  # keep the tensors alive while the graph exists
+        fd = None
+        handles = (ctypes.c_void_p * max(n, 1))()
+        modes = (ctypes.c_int * max(n, 1))()
+        ranks = (ctypes.c_int * max(n, 1))()
+        outs = (ctypes.c_void_p * max(n, 1))()
+        fptrs = (ctypes.c_void_p * max(n, 1))()
+        self._fptr_arrays = []
+        for i, (at, mode, factors, out) in enumerate(items):
+            handles[i] = at._h.value
+            modes[i] = mode
+            ref = next(f for m, f in enumerate(factors) if f is not None and (m != mode or at.N == 1))
+            ranks[i] = int(ref.shape[1])
+            fd = _fdtype(ref) if fd is None else fd
+            arr = (ctypes.c_void_p * at.N)(*[(f.data_ptr() if f is not None else 0) for f in factors])
+            self._fptr_arrays.append(arr)
+            fptrs[i] = ctypes.cast(arr, ctypes.c_void_p).value
+            outs[i] = out.data_ptr()
+        var = None
+        if variants is not None:
+            var = (ctypes.c_int * max(n, 1))(*[int(v) for v in variants])
+        h = ctypes.c_void_p()
+        self._h = None
+        _check(lib().alto_batch_create(ctypes.byref(h), n, handles, modes, fptrs, ranks,
+                                       fd if fd is not None else F32, outs, var, _stream(stream)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().alto_batch_run(self._h, _stream(stream)))
+
+    def info(self):
+        a, g, s, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().alto_batch_info(self._h, ctypes.byref(a), ctypes.byref(g), ctypes.byref(s), ctypes.byref(k)))
+        return dict(items=a.value, groups=g.value, single=s.value, kernels=k.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().alto_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class AltoTensor:
@@ -247,8 +314,26 @@ class AltoTensor:
         _check(lib().alto_export(self._h, vp(keys), vp(perm), vp(vals), vp(bounds), vp(ivl)))
         return dict(keys=keys, perm=perm, vals=vals, bounds=bounds, intervals=ivl)
 
+    def mode_stats(self, mode):
+        """[I_n, distinct, reuse, max interval, hot rows, hot share, median and
+        90th-percentile unit interval width]."""
+        out = (ctypes.c_double * 8)()
+        _check(lib().alto_get_mode_stats(self._h, mode, out, 8))
+        return list(out)
+
+    def unit_fit(self, mode, rows):
+        f = ctypes.c_double()
+        _check(lib().alto_get_unit_fit(self._h, mode, int(rows), ctypes.byref(f)))
+        return f.value
+
     def set_variant(self, mode, variant):
         _check(lib().alto_set_variant(self._h, mode, int(variant)))
+
+    def resolve_variant(self, mode, rank, fdtype=F32, variant=0):
+        """The variant an MTTKRP of this mode and rank runs for ``variant``."""
+        v = ctypes.c_int()
+        _check(lib().alto_resolve_variant(self._h, mode, int(rank), int(fdtype), int(variant), ctypes.byref(v)))
+        return v.value
 
     def check(self, stream=None):
         _check(lib().alto_check(self._h, _stream(stream)))

@@ -31,6 +31,7 @@ alto_status fail(alto_status code, const char* fmt, ...) {
 }
 
 void note_launch(int k) { g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed); }
+uint64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t prof_begin(alto_tensor_s* t, int mode, cudaStream_t s) {
   if (!t->prof) return cudaSuccess;
@@ -354,9 +355,14 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
         return x.first != y.first ? x.first > y.first : x.second < y.second;
       });
       std::vector<uint32_t> rows;
+      double hot_samples = 0.0;
       for (int k = 0; k < nh; ++k)
-        if (pr[k].second != 0xffffffffu) rows.push_back(pr[k].second);  // that value marks empty slots
+        if (pr[k].second != 0xffffffffu) {  // that value marks empty slots
+          rows.push_back(pr[k].second);
+          hot_samples += pr[k].first;
+        }
       nh = static_cast<int>(rows.size());
+      t->hot_share[n] = hot_samples / static_cast<double>((nnz + kHotSample - 1) / kHotSample);
       ALLOC(t->hot[n], uint32_t*, sizeof(uint32_t) * (nh > 0 ? nh : 1));
       CK(cudaMemcpyAsync(t->hot[n], rows.data(), sizeof(uint32_t) * nh, cudaMemcpyHostToDevice, s));
       CK(cudaStreamSynchronize(s));
@@ -498,6 +504,27 @@ alto_status alto_get_hot_rows(alto_t t, int mode, uint32_t* rows, int* count) {
         cudaMemcpy(rows, t->hot[mode], sizeof(uint32_t) * t->hot_n[mode], cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(ALTO_ECUDA, "hot rows: %s", cudaGetErrorString(e));
   }
+  return ALTO_OK;
+}
+
+alto_status alto_get_mode_stats(alto_t t, int mode, double* out, int n) {
+  if (t == nullptr || out == nullptr) return fail(ALTO_EINVAL, "null argument");
+  if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
+  const std::vector<uint32_t>& w = t->unit_width_sorted[mode];
+  const double med = w.empty() ? 0.0 : static_cast<double>(w[w.size() / 2]);
+  const double p90 = w.empty() ? 0.0 : static_cast<double>(w[(w.size() * 9) / 10]);
+  const double v[8] = {static_cast<double>(t->lay.dims[mode]), static_cast<double>(t->distinct[mode]), t->reuse[mode],
+                       static_cast<double>(t->max_ivl[mode]), static_cast<double>(t->hot_n[mode]), t->hot_share[mode],
+                       med, p90};
+  for (int i = 0; i < n && i < 8; ++i) out[i] = v[i];
+  for (int i = 8; i < n; ++i) out[i] = 0.0;
+  return ALTO_OK;
+}
+
+alto_status alto_get_unit_fit(alto_t t, int mode, uint64_t rows, double* frac) {
+  if (t == nullptr || frac == nullptr) return fail(ALTO_EINVAL, "null argument");
+  if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
+  *frac = t->unit_fit_frac(mode, rows);
   return ALTO_OK;
 }
 

@@ -78,6 +78,7 @@ struct alto_tensor_s {
   uint32_t* ivl = nullptr;    // L x N x 2 closed intervals
   uint32_t* hot[alto::kMaxModes] = {};  // hot rows per mode, hottest first
   int hot_n[alto::kMaxModes] = {};
+  double hot_share[alto::kMaxModes] = {};  // sampled nonzeros in the hot rows / all samples
   void* hot_rep = nullptr;              // MTTKRP hot-row replicas (lazy)
   size_t hot_rep_bytes = 0;
   int* status = nullptr;      // device status word
@@ -116,6 +117,7 @@ namespace alto {
 
 // process-wide count of kernel launches issued by the library
 void note_launch(int k = 1);
+uint64_t launch_total();
 
 // MTTKRP event timing: record the start / stop of one timed call
 cudaError_t prof_begin(alto_tensor_s* t, int mode, cudaStream_t s);

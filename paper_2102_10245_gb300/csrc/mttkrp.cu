@@ -46,8 +46,8 @@ int auto_variant(const alto_tensor_s* t, int mode, int R, size_t osz) {
   return ALTO_VAR_WARPAGG;
 }
 
-alto_status run_mttkrp(alto_tensor_s* t, int mode, const void* const* factors, int R,
-                       alto_dtype fdtype, void* out, int variant, cudaStream_t s) {
+alto_status check_mttkrp_args(const alto_tensor_s* t, int mode, const void* const* factors, int R,
+                              alto_dtype fdtype, const void* out, int variant) {
   const Layout& lay = t->lay;
   const int N = lay.N;
   if (mode < 0 || mode >= N) return fail(ALTO_EINVAL, "mode %d outside [0, %d)", mode, N);
@@ -63,6 +63,52 @@ alto_status run_mttkrp(alto_tensor_s* t, int mode, const void* const* factors, i
     return fail(ALTO_EINVAL, "bad factor dtype %d", static_cast<int>(fdtype));
   }
   if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  return ALTO_OK;
+}
+
+// The variant an MTTKRP call runs: the call's, else the tensor's per-mode
+// override, else the automatic rule.
+int resolve_variant(const alto_tensor_s* t, int mode, int R, size_t osz, int variant) {
+  int v = variant != ALTO_VAR_AUTO ? variant : t->variant[mode];
+  if (v == ALTO_VAR_AUTO) v = auto_variant(t, mode, R, osz);
+  return v;
+}
+
+// Arguments common to every variant.
+void fill_launch(const alto_tensor_s* t, int mode, const void* const* factors, int R, void* out,
+                 MttkrpLaunch* l) {
+  const Layout& lay = t->lay;
+  const int N = lay.N;
+  int slot_mode[kMaxModes];
+  int k = 0;
+  for (int m = 0; m < N; ++m)
+    if (m != mode) slot_mode[k++] = m;
+  slot_mode[k] = mode;
+  make_decode(lay, slot_mode, &l->args.dp);
+  l->args.keys = t->keys;
+  l->args.vals = t->vals;
+  l->args.M = t->M;
+  l->args.L = t->L;
+  for (int sl = 0; sl < N; ++sl) l->args.f[sl] = factors[slot_mode[sl]];
+  l->args.out = out;
+  l->args.R = R;
+  l->args.out_mode = mode;
+  l->args.ivl = t->ivl;
+  l->N = N;
+  l->KW = lay.KW;
+  l->sms = device_sms();
+}
+
+size_t smem_temp_bytes(const alto_tensor_s* t, int mode, int R, size_t osz, int* rows_out) {
+  const int rows = smem_rows_for(t, mode, R, osz);
+  *rows_out = rows;
+  return static_cast<size_t>(rows) * R * osz + static_cast<size_t>((rows + 31) / 32) * 4;
+}
+
+alto_status run_mttkrp(alto_tensor_s* t, int mode, const void* const* factors, int R,
+                       alto_dtype fdtype, void* out, int variant, cudaStream_t s) {
+  alto_status st = check_mttkrp_args(t, mode, factors, R, fdtype, out, variant);
+  if (st != ALTO_OK) return st;
   const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
   cudaError_t e = prof_begin(t, mode, s);
   if (e != cudaSuccess) return fail(ALTO_ECUDA, "profiling event: %s", cudaGetErrorString(e));
@@ -81,28 +127,9 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
   if (e != cudaSuccess) return e;
   if (t->M == 0) return cudaSuccess;
 
-  int v = variant != ALTO_VAR_AUTO ? variant : t->variant[mode];
-  if (v == ALTO_VAR_AUTO) v = auto_variant(t, mode, R, osz);
-
+  int v = resolve_variant(t, mode, R, osz, variant);
   MttkrpLaunch l{};
-  int slot_mode[kMaxModes];
-  int k = 0;
-  for (int m = 0; m < N; ++m)
-    if (m != mode) slot_mode[k++] = m;
-  slot_mode[k] = mode;
-  make_decode(lay, slot_mode, &l.args.dp);
-  l.args.keys = t->keys;
-  l.args.vals = t->vals;
-  l.args.M = t->M;
-  l.args.L = t->L;
-  for (int sl = 0; sl < N; ++sl) l.args.f[sl] = factors[slot_mode[sl]];
-  l.args.out = out;
-  l.args.R = R;
-  l.args.out_mode = mode;
-  l.args.ivl = t->ivl;
-  l.N = N;
-  l.KW = lay.KW;
-  l.sms = device_sms();
+  fill_launch(t, mode, factors, R, out, &l);
   if (v == ALTO_VAR_TEMP) return launch_temp_variant(t, l, fdtype, osz, s);
   if (!mttkrp_specialised(N, R)) v = ALTO_VAR_ATOMIC;  // the generic kernel
   l.variant = v;
@@ -131,9 +158,9 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
     }
   }
   if (v == ALTO_VAR_SMEM) {
-    const int rows = smem_rows_for(t, mode, R, osz);
+    int rows = 0;
+    l.smem_dyn = smem_temp_bytes(t, mode, R, osz, &rows);
     l.args.smem_rows = rows;
-    l.smem_dyn = static_cast<size_t>(rows) * R * osz + static_cast<size_t>((rows + 31) / 32) * 4;
   }
   e = mttkrp_dispatch(l, fdtype, s);
   if (e != cudaSuccess || H == 0) return e;
@@ -141,12 +168,29 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
   const unsigned g = static_cast<unsigned>((total + 255) / 256);
   if (osz == 8)
     hot_reduce_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(t->hot_rep), t->hot[mode], H, R,
-                                                static_cast<double*>(out));
+                                                kHotReplicas, static_cast<double*>(out));
   else
     hot_reduce_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(t->hot_rep), t->hot[mode], H, R,
-                                               static_cast<float*>(out));
+                                               kHotReplicas, static_cast<float*>(out));
   note_launch();
   return cudaGetLastError();
 }
 
 }  // namespace alto
+
+using namespace alto;
+
+extern "C" alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_dtype fdtype, int variant,
+                                            int* out) {
+  if (t == nullptr || out == nullptr) return fail(ALTO_EINVAL, "null argument");
+  if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "mode %d outside [0, %d)", mode, t->lay.N);
+  if (rank < 1) return fail(ALTO_EINVAL, "rank %d < 1", rank);
+  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  if (fdtype != ALTO_F64 && fdtype != ALTO_F32 && fdtype != ALTO_BF16)
+    return fail(ALTO_EINVAL, "bad factor dtype %d", static_cast<int>(fdtype));
+  const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
+  int v = resolve_variant(t, mode, rank, osz, variant);
+  if (v != ALTO_VAR_TEMP && !mttkrp_specialised(t->lay.N, rank)) v = ALTO_VAR_ATOMIC;
+  *out = v;
+  return ALTO_OK;
+}

@@ -215,6 +215,7 @@ __device__ __forceinline__ int hot_lookup(const uint32_t* keys, const uint32_t* 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 constexpr int kUnitSegs = 8;  // segments per thread-block unit
+static_assert(sizeof(MttkrpArgs) % 4 == 0, "MttkrpArgs is copied as 32-bit words");
 
 // staged tuple: N indices and the value, padded to 16-byte words
 template <int N, typename VT>
@@ -332,252 +333,353 @@ __device__ __forceinline__ void flush_shared(typename FTraits<FT>::AT* rowp, int
 }
 
 // ---------------------------------------------------------------------------
-// The kernel.
+// Per-block state of one MTTKRP (hot-row table, replica).
+template <typename AT>
+struct BlockState {
+  int H;
+  AT* hdata;
+  uint32_t* hkeys;
+  uint32_t* hidx;
+};
+
+// Build the block's hot-row hash table in shared memory (WARPAGG).
+template <typename AT, int R>
+__device__ __forceinline__ BlockState<AT> hot_table(const MttkrpArgs& a, unsigned char* dyn, int replica) {
+  BlockState<AT> st{0, nullptr, nullptr, nullptr};
+  st.H = a.hot_n;
+  if (st.H > 0) {
+    const int TS = 1 << a.hot_bits;
+    st.hdata = static_cast<AT*>(a.hot_rep) + static_cast<size_t>(replica) * st.H * R;
+    st.hkeys = reinterpret_cast<uint32_t*>(dyn);
+    st.hidx = st.hkeys + TS;
+    for (int i = threadIdx.x; i < TS; i += kThreads) st.hkeys[i] = kHotEmpty;
+    __syncthreads();
+    const uint32_t mask = static_cast<uint32_t>(TS - 1);
+    for (int i = threadIdx.x; i < st.H; i += kThreads) {
+      const uint32_t row = a.hot[i];
+      uint32_t h = hot_hash(row, a.hot_bits);
+      for (int probe = 0; probe < TS; ++probe) {
+        if (atomicCAS(st.hkeys + h, kHotEmpty, row) == kHotEmpty) {
+          st.hidx[h] = static_cast<uint32_t>(i);
+          break;
+        }
+        h = (h + 1) & mask;
+      }
+    }
+  }
+  __syncthreads();
+  return st;
+}
+
+// One thread-block unit (8 consecutive segments) of one MTTKRP.  All threads
+// of the block call it together.
 template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads, 5) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+__device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
+                                             const BlockState<typename FTraits<FT>::AT>& st,
+                                             uint4 (*s_stage)[32][Stage<N, typename FTraits<FT>::VT>::W4],
+                                             uint32_t* s_lorows, unsigned char* dyn) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   using C = Cols<R, FT>;
   constexpr int LPN = C::LPN;
   constexpr int PER = LPN;             // staged positions per group (32 / groups)
   constexpr int K = C::CPL;
-  constexpr int W4 = Stage<N, VT>::W4;
   constexpr bool AGG = POL != kAtomic;  // reorder by output row before the gathers
-  __shared__ uint4 s_stage[kWarps][32][W4];
-  __shared__ uint32_t s_lo, s_rows;
-  extern __shared__ __align__(16) unsigned char dyn[];
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / LPN, c = lane % LPN;
   const uint32_t lt = lanemask_lt();
   AT* out = static_cast<AT*>(a.out);
-  const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
+  const int H = st.H;
 
-  // WARPAGG: the block's hot-row table (keys, slot index) and its replica
-  int H = 0;
-  AT* hdata = nullptr;
-  uint32_t* hkeys = nullptr;
-  uint32_t* hidx = nullptr;
-  if constexpr (POL == kWarpAgg) {
-    H = a.hot_n;
-    if (H > 0) {
-      const int TS = 1 << a.hot_bits;
-      hdata = static_cast<AT*>(a.hot_rep) + static_cast<size_t>(blockIdx.x % kHotReplicas) * H * R;
-      hkeys = reinterpret_cast<uint32_t*>(dyn);
-      hidx = hkeys + TS;
-      for (int i = threadIdx.x; i < TS; i += kThreads) hkeys[i] = kHotEmpty;
-      __syncthreads();
-      const uint32_t mask = static_cast<uint32_t>(TS - 1);
-      for (int i = threadIdx.x; i < H; i += kThreads) {
-        const uint32_t row = a.hot[i];
-        uint32_t h = hot_hash(row, a.hot_bits);
-        for (int probe = 0; probe < TS; ++probe) {
-          if (atomicCAS(hkeys + h, kHotEmpty, row) == kHotEmpty) {
-            hidx[h] = static_cast<uint32_t>(i);
-            break;
-          }
-          h = (h + 1) & mask;
+  const int64_t useg1 = (u + 1) * kUnitSegs < a.L ? (u + 1) * kUnitSegs : a.L;
+  const int64_t ub = seg_begin(u * kUnitSegs, a.M, a.L), ue = seg_begin(useg1, a.M, a.L);
+
+  // destination of this unit
+  AT* dst = out;
+  uint32_t lo = 0;
+  bool use_smem = false;
+  if constexpr (POL == kSmem) {
+    if (warp == 0) {
+      const int64_t seg = u * kUnitSegs + lane;
+      uint32_t l0 = 0xffffffffu, h0 = 0;
+      if (lane < kUnitSegs && seg < a.L) {
+        const int Nm = a.dp.nmodes;
+        const uint32_t s0 = a.ivl[(seg * Nm + a.out_mode) * 2], e0 = a.ivl[(seg * Nm + a.out_mode) * 2 + 1];
+        if (e0 >= s0) {
+          l0 = s0;
+          h0 = e0;
         }
       }
-      __syncthreads();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        l0 = min(l0, __shfl_xor_sync(0xffffffffu, l0, o));
+        h0 = max(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+      }
+      if (lane == 0) {
+        s_lorows[0] = l0;
+        s_lorows[1] = (h0 >= l0) ? h0 - l0 + 1 : 0;
+      }
     }
+    __syncthreads();
+    lo = s_lorows[0];
+    const uint32_t rows = s_lorows[1];
+    use_smem = rows <= static_cast<uint32_t>(a.smem_rows);
+    if (use_smem) {
+      AT* temp = reinterpret_cast<AT*>(dyn);
+      uint32_t* touched = reinterpret_cast<uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
+      for (uint32_t i = threadIdx.x; i < rows * R; i += kThreads) temp[i] = AT(0);
+      for (uint32_t i = threadIdx.x; i < (rows + 31) / 32; i += kThreads) touched[i] = 0;
+      dst = temp;
+    }
+    __syncthreads();
+  } else if constexpr (POL == kTemp) {
+    dst = static_cast<AT*>(a.temp) + a.toff[u];
+    lo = a.ulo[u];
   }
 
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t useg1 = (u + 1) * kUnitSegs < a.L ? (u + 1) * kUnitSegs : a.L;
-    const int64_t ub = seg_begin(u * kUnitSegs, a.M, a.L), ue = seg_begin(useg1, a.M, a.L);
-
-    // destination of this unit
-    AT* dst = out;
-    uint32_t lo = 0;
-    bool use_smem = false;
-    if constexpr (POL == kSmem) {
-      if (warp == 0) {
-        const int64_t seg = u * kUnitSegs + lane;
-        uint32_t l0 = 0xffffffffu, h0 = 0;
-        if (lane < kUnitSegs && seg < a.L) {
-          const int Nm = a.dp.nmodes;
-          const uint32_t s0 = a.ivl[(seg * Nm + a.out_mode) * 2], e0 = a.ivl[(seg * Nm + a.out_mode) * 2 + 1];
-          if (e0 >= s0) {
-            l0 = s0;
-            h0 = e0;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          l0 = min(l0, __shfl_xor_sync(0xffffffffu, l0, o));
-          h0 = max(h0, __shfl_xor_sync(0xffffffffu, h0, o));
-        }
-        if (lane == 0) {
-          s_lo = l0;
-          s_rows = (h0 >= l0) ? h0 - l0 + 1 : 0;
-        }
-      }
-      __syncthreads();
-      lo = s_lo;
-      const uint32_t rows = s_rows;
-      use_smem = rows <= static_cast<uint32_t>(a.smem_rows);
-      if (use_smem) {
-        AT* temp = reinterpret_cast<AT*>(dyn);
-        uint32_t* touched = reinterpret_cast<uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
-        for (uint32_t i = threadIdx.x; i < rows * R; i += kThreads) temp[i] = AT(0);
-        for (uint32_t i = threadIdx.x; i < (rows + 31) / 32; i += kThreads) touched[i] = 0;
-        dst = temp;
-      }
-      __syncthreads();
-    } else if constexpr (POL == kTemp) {
-      dst = static_cast<AT*>(a.temp) + a.toff[u];
-      lo = a.ulo[u];
+  // chunks of this unit: warp w takes w, w + 8, ...
+  int64_t base = ub + static_cast<int64_t>(warp) * 32;
+  KeyT<KW> kn{};
+  VT vn = VT(0);
+  if (base + lane < ue) {
+    kn = load_key<KW>(a.keys, base + lane);
+    vn = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
+  }
+  for (; base < ue; base += kWarps * 32) {
+    const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
+    const bool ok = lane < cnt;
+    const KeyT<KW> k = kn;
+    const VT v = vn;
+    const int64_t nb = base + kWarps * 32;
+    if (nb + lane < ue) {  // prefetch the warp's next chunk
+      kn = load_key<KW>(a.keys, nb + lane);
+      vn = __ldcs(static_cast<const VT*>(a.vals) + nb + lane);
     }
-
-    // chunks of this unit: warp w takes w, w + 8, ...
-    int64_t base = ub + static_cast<int64_t>(warp) * 32;
-    KeyT<KW> kn{};
-    VT vn = VT(0);
-    if (base + lane < ue) {
-      kn = load_key<KW>(a.keys, base + lane);
-      vn = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
+    uint32_t id[N];
+#pragma unroll
+    for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
+    if constexpr (POL == kWarpAgg) {
+      // hot rows are staged as (bit 31 | table slot); the host enables the
+      // table only when every output row is below 2^31.  Only nonzeros
+      // whose key carries the hot-row flag probe the table.
+      if (H > 0 && ok && (a.hot_key_bit < 0 || key_bit<KW>(k, a.hot_key_bit))) {
+        const int slot = hot_lookup(st.hkeys, st.hidx, id[N - 1], a.hot_bits);
+        if (slot >= 0) id[N - 1] = 0x80000000u | static_cast<uint32_t>(slot);
+      }
     }
-    for (; base < ue; base += kWarps * 32) {
-      const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
-      const bool ok = lane < cnt;
-      const KeyT<KW> k = kn;
-      const VT v = vn;
-      const int64_t nb = base + kWarps * 32;
-      if (nb + lane < ue) {  // prefetch the warp's next chunk
-        kn = load_key<KW>(a.keys, nb + lane);
-        vn = __ldcs(static_cast<const VT*>(a.vals) + nb + lane);
-      }
-      uint32_t id[N];
+    int pos = lane;
+    if constexpr (AGG) {
+      const unsigned long long tag = ok ? static_cast<unsigned long long>(id[N - 1]) : (0x100000000ull + lane);
+      const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+      const int leader = __ffs(peers) - 1;
+      const uint32_t sz = (lane == leader) ? __popc(peers) : 0u;
+      uint32_t inc = sz;
 #pragma unroll
-      for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
-      if constexpr (POL == kWarpAgg) {
-        // hot rows are staged as (bit 31 | table slot); the host enables the
-        // table only when every output row is below 2^31.  Only nonzeros
-        // whose key carries the hot-row flag probe the table.
-        if (H > 0 && ok && (a.hot_key_bit < 0 || key_bit<KW>(k, a.hot_key_bit))) {
-          const int slot = hot_lookup(hkeys, hidx, id[N - 1], a.hot_bits);
-          if (slot >= 0) id[N - 1] = 0x80000000u | static_cast<uint32_t>(slot);
-        }
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
       }
-      int pos = lane;
-      if constexpr (AGG) {
-        const unsigned long long tag = ok ? static_cast<unsigned long long>(id[N - 1]) : (0x100000000ull + lane);
-        const uint32_t peers = __match_any_sync(0xffffffffu, tag);
-        const int leader = __ffs(peers) - 1;
-        const uint32_t sz = (lane == leader) ? __popc(peers) : 0u;
-        uint32_t inc = sz;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += y;
-        }
-        const uint32_t start = __shfl_sync(0xffffffffu, inc - sz, leader);
-        pos = static_cast<int>(start + __popc(peers & lt));
-      }
-      if (ok) stage_store<N, VT>(s_stage[warp][pos], id, v);
-      __syncwarp();
+      const uint32_t start = __shfl_sync(0xffffffffu, inc - sz, leader);
+      pos = static_cast<int>(start + __popc(peers & lt));
+    }
+    if (ok) stage_store<N, VT>(s_stage[warp][pos], id, v);
+    __syncwarp();
 
-      // group g: positions g*PER .. g*PER + PER - 1, gathers one position
-      // ahead.  Loads past the chunk's end read its last valid slot again
-      // (harmless, the result is not used), so every load is unconditional
-      // and the pipeline registers rename instead of being copied.
-      const int p0 = g * PER;
-      Pos<N, VT> cur = stage_load<N, VT>(s_stage[warp][p0 < cnt ? p0 : cnt - 1]);
-      Rows<N, R, FT> rc;
-      gather<N, R, FT>(a, cur, c, rc);
-      AT acc[K];
+    // group g: positions g*PER .. g*PER + PER - 1, gathers one position
+    // ahead.  Loads past the chunk's end read its last valid slot again
+    // (harmless, the result is not used), so every load is unconditional
+    // and the pipeline registers rename instead of being copied.
+    const int p0 = g * PER;
+    Pos<N, VT> cur = stage_load<N, VT>(s_stage[warp][p0 < cnt ? p0 : cnt - 1]);
+    Rows<N, R, FT> rc;
+    gather<N, R, FT>(a, cur, c, rc);
+    AT acc[K];
 #pragma unroll
-      for (int e = 0; e < K; ++e) acc[e] = AT(0);
+    for (int e = 0; e < K; ++e) acc[e] = AT(0);
 #pragma unroll
-      for (int j = 0; j < PER; ++j) {
-        const int p = p0 + j;
-        const bool has = p < cnt;
-        const bool hasn = (j + 1 < PER) && (p + 1 < cnt);
-        Pos<N, VT> nxt;
-        Rows<N, R, FT> rn;
-        if (j + 1 < PER) {
-          nxt = stage_load<N, VT>(s_stage[warp][p + 1 < cnt ? p + 1 : cnt - 1]);
-          gather<N, R, FT>(a, nxt, c, rn);
-        }
-        if (has) {
-          const uint32_t row = cur.id[N - 1];
-          if constexpr (POL == kAtomic) {
-            AT t[K];
-            product<N, R, FT>(cur, rc, t);
-            flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, t);
-          } else {
-            accumulate<N, R, FT>(cur, rc, acc);
-            if (!hasn || nxt.id[N - 1] != row) {
-              if constexpr (POL == kSmem) {
-                if (use_smem) {
-                  flush_shared<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
-                  if (c == 0) {
-                    uint32_t* touched = reinterpret_cast<uint32_t*>(reinterpret_cast<AT*>(dyn) +
-                                                                    static_cast<size_t>(a.smem_rows) * R);
-                    atomicOr(touched + ((row - lo) >> 5), 1u << ((row - lo) & 31));
-                  }
-                } else {
-                  flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
+    for (int j = 0; j < PER; ++j) {
+      const int p = p0 + j;
+      const bool has = p < cnt;
+      const bool hasn = (j + 1 < PER) && (p + 1 < cnt);
+      Pos<N, VT> nxt;
+      Rows<N, R, FT> rn;
+      if (j + 1 < PER) {
+        nxt = stage_load<N, VT>(s_stage[warp][p + 1 < cnt ? p + 1 : cnt - 1]);
+        gather<N, R, FT>(a, nxt, c, rn);
+      }
+      if (has) {
+        const uint32_t row = cur.id[N - 1];
+        if constexpr (POL == kAtomic) {
+          AT t[K];
+          product<N, R, FT>(cur, rc, t);
+          flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, t);
+        } else {
+          accumulate<N, R, FT>(cur, rc, acc);
+          if (!hasn || nxt.id[N - 1] != row) {
+            if constexpr (POL == kSmem) {
+              if (use_smem) {
+                flush_shared<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
+                if (c == 0) {
+                  uint32_t* touched = reinterpret_cast<uint32_t*>(reinterpret_cast<AT*>(dyn) +
+                                                                  static_cast<size_t>(a.smem_rows) * R);
+                  atomicOr(touched + ((row - lo) >> 5), 1u << ((row - lo) & 31));
                 }
-              } else if constexpr (POL == kWarpAgg) {
-                if (row & 0x80000000u)
-                  flush_global<R, FT>(hdata + static_cast<size_t>(row & 0x7fffffffu) * R, c, acc);
-                else
-                  flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
               } else {
-                flush_global<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
+                flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
               }
-#pragma unroll
-              for (int e = 0; e < K; ++e) acc[e] = AT(0);
+            } else if constexpr (POL == kWarpAgg) {
+              if (row & 0x80000000u)
+                flush_global<R, FT>(st.hdata + static_cast<size_t>(row & 0x7fffffffu) * R, c, acc);
+              else
+                flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, acc);
+            } else {
+              flush_global<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
             }
-          }
-        }
-        if (j + 1 < PER) {
-          cur = nxt;
-          rc = rn;
-        }
-      }
-      __syncwarp();
-    }
-
-    if constexpr (POL == kSmem) {
-      __syncthreads();
-      if (use_smem) {
-        const AT* temp = reinterpret_cast<const AT*>(dyn);
-        const uint32_t* touched = reinterpret_cast<const uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
-        const uint32_t rows = s_rows;
-        const int cc = threadIdx.x % LPN;
-        for (uint32_t w = threadIdx.x / LPN; w < rows; w += kThreads / LPN) {
-          if ((touched[w >> 5] >> (w & 31)) & 1u) {
-            AT vals[K];
 #pragma unroll
-            for (int q = 0; q < C::PAIRS; ++q)
-#pragma unroll
-              for (int e = 0; e < C::VEC; ++e)
-                vals[q * C::VEC + e] = temp[static_cast<size_t>(w) * R + cc * C::VEC + q * C::STRIDE + e];
-            flush_global<R, FT>(out + static_cast<size_t>(lo + w) * R, cc, vals);
+            for (int e = 0; e < K; ++e) acc[e] = AT(0);
           }
         }
       }
-      __syncthreads();
+      if (j + 1 < PER) {
+        cur = nxt;
+        rc = rn;
+      }
     }
+    __syncwarp();
   }
 
+  if constexpr (POL == kSmem) {
+    __syncthreads();
+    if (use_smem) {
+      const AT* temp = reinterpret_cast<const AT*>(dyn);
+      const uint32_t* touched = reinterpret_cast<const uint32_t*>(temp + static_cast<size_t>(a.smem_rows) * R);
+      const uint32_t rows = s_lorows[1];
+      const int cc = threadIdx.x % LPN;
+      for (uint32_t w = threadIdx.x / LPN; w < rows; w += kThreads / LPN) {
+        if ((touched[w >> 5] >> (w & 31)) & 1u) {
+          AT vals[K];
+#pragma unroll
+          for (int q = 0; q < C::PAIRS; ++q)
+#pragma unroll
+            for (int e = 0; e < C::VEC; ++e)
+              vals[q * C::VEC + e] = temp[static_cast<size_t>(w) * R + cc * C::VEC + q * C::STRIDE + e];
+          flush_global<R, FT>(out + static_cast<size_t>(lo + w) * R, cc, vals);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One MTTKRP: persistent blocks stride over the units.
+template <int N, int KW, int R, typename FT, int POL>
+__global__ void __launch_bounds__(kThreads, 5) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+  using AT = typename FTraits<FT>::AT;
+  using VT = typename FTraits<FT>::VT;
+  __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
+  __shared__ uint32_t s_lorows[2];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  BlockState<AT> st{0, nullptr, nullptr, nullptr};
+  if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(a, dyn, blockIdx.x % kHotReplicas);
+  const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x)
+    process_unit<N, KW, R, FT, POL>(a, u, st, s_stage, s_lorows, dyn);
+}
+
+// Many MTTKRPs of one kernel shape in one persistent launch (the batched
+// entry point): items[i] describes MTTKRP i, unit_prefix[i] its first global
+// unit.  Each block takes a contiguous range of global units, so it switches
+// items rarely; on a switch it copies the item's description to shared
+// memory and rebuilds its hot-row table.
+struct BatchArgs {
+  const MttkrpArgs* items;
+  const int64_t* unit_prefix;  // nitems + 1
+  int nitems;
+  int hot_replicas;            // copies of each item's hot rows
+};
+
+template <int N, int KW, int R, typename FT, int POL>
+__global__ void __launch_bounds__(kThreads, 5) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
+  using AT = typename FTraits<FT>::AT;
+  using VT = typename FTraits<FT>::VT;
+  __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
+  __shared__ uint32_t s_lorows[2];
+  __shared__ __align__(16) MttkrpArgs s_args;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int64_t total = b.unit_prefix[b.nitems];
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t g0 = static_cast<int64_t>(blockIdx.x) * per;
+  const int64_t g1 = g0 + per < total ? g0 + per : total;
+  if (g0 >= g1) return;
+  // item of the first unit: binary search over the prefix
+  int lo = 0, hi = b.nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.unit_prefix[mid] <= g0) lo = mid; else hi = mid - 1;
+  }
+  int item = -1;
+  BlockState<AT> st{0, nullptr, nullptr, nullptr};
+  for (int64_t gu = g0; gu < g1; ++gu) {
+    int want = item < 0 ? lo : item;
+    while (gu >= b.unit_prefix[want + 1]) ++want;
+    if (want != item) {
+      item = want;
+      __syncthreads();
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(b.items + item);
+      uint32_t* d = reinterpret_cast<uint32_t*>(&s_args);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(MttkrpArgs) / 4); i += kThreads) d[i] = src[i];
+      __syncthreads();
+      if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(s_args, dyn, blockIdx.x % b.hot_replicas);
+    }
+    process_unit<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage, s_lorows, dyn);
+  }
 }
 
 // out[hot[h], :] = sum over the replicas of rep[k, h, :] (every contribution
 // to a row in the hot table went to the replicas, none to the output)
 template <typename AT>
 __global__ void __launch_bounds__(256) hot_reduce_kernel(const AT* __restrict__ rep, const uint32_t* __restrict__ hot,
-                                                         int H, int R, AT* __restrict__ out) {
+                                                         int H, int R, int nrep, AT* __restrict__ out) {
   const int total = H * R;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     AT s = AT(0);
-#pragma unroll 8
-    for (int k = 0; k < kHotReplicas; ++k) s += rep[static_cast<size_t>(k) * total + e];
+    for (int k = 0; k < nrep; ++k) s += rep[static_cast<size_t>(k) * total + e];
     const int h = e / R, r = e - h * R;
     out[static_cast<size_t>(hot[h]) * R + r] = s;
+  }
+}
+
+// The same for many MTTKRPs at once: item i owns elements
+// [prefix[i], prefix[i+1]) of the flattened (row, column) space.
+struct HotItem {
+  const void* rep;
+  const uint32_t* hot;
+  void* out;
+  int H;
+  int R;
+  int nrep;
+  int pad;
+};
+
+template <typename AT>
+__global__ void __launch_bounds__(256) hot_reduce_batch_kernel(const HotItem* __restrict__ items,
+                                                               const int64_t* __restrict__ prefix, int n) {
+  const int64_t total = prefix[n];
+  for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const HotItem it = items[lo];
+    const int64_t q = e - prefix[lo];
+    const int64_t tot = static_cast<int64_t>(it.H) * it.R;
+    const AT* rep = static_cast<const AT*>(it.rep);
+    AT s = AT(0);
+    for (int k = 0; k < it.nrep; ++k) s += rep[k * tot + q];
+    const int64_t h = q / it.R, r = q - h * it.R;
+    static_cast<AT*>(it.out)[static_cast<size_t>(it.hot[h]) * it.R + r] = s;
   }
 }
 
@@ -637,6 +739,82 @@ cudaError_t mttkrp_dispatch_f64_k2(const MttkrpLaunch& l, cudaStream_t s);
 cudaError_t mttkrp_dispatch_bf16_k1(const MttkrpLaunch& l, cudaStream_t s);
 cudaError_t mttkrp_dispatch_bf16_k2(const MttkrpLaunch& l, cudaStream_t s);
 
+// launch description of one group of the batched entry point
+struct BatchLaunch {
+  BatchArgs args;
+  int N;
+  int KW;
+  int R;
+  int variant;   // ATOMIC / WARPAGG / SMEM
+  int sms;
+  size_t smem_dyn;
+};
+
+cudaError_t mttkrp_batch_dispatch_f32_k1(const BatchLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_batch_dispatch_f32_k2(const BatchLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_batch_dispatch_f64_k1(const BatchLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_batch_dispatch_f64_k2(const BatchLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_batch_dispatch_bf16_k1(const BatchLaunch& l, cudaStream_t s);
+cudaError_t mttkrp_batch_dispatch_bf16_k2(const BatchLaunch& l, cudaStream_t s);
+
+inline cudaError_t mttkrp_batch_dispatch(const BatchLaunch& l, alto_dtype fdtype, cudaStream_t s) {
+  switch (fdtype) {
+    case ALTO_F64: return l.KW == 1 ? mttkrp_batch_dispatch_f64_k1(l, s) : mttkrp_batch_dispatch_f64_k2(l, s);
+    case ALTO_F32: return l.KW == 1 ? mttkrp_batch_dispatch_f32_k1(l, s) : mttkrp_batch_dispatch_f32_k2(l, s);
+    default: return l.KW == 1 ? mttkrp_batch_dispatch_bf16_k1(l, s) : mttkrp_batch_dispatch_bf16_k2(l, s);
+  }
+}
+
+template <typename Kern>
+cudaError_t launch_batch(Kern kern, const BatchLaunch& l, cudaStream_t s) {
+  // the default dynamic limit is 48 KB minus the kernel's static shared
+  // memory: raise it for every launch that uses dynamic shared memory
+  if (l.smem_dyn > 0) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(l.smem_dyn));
+    if (e != cudaSuccess) return e;
+  }
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, l.smem_dyn);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  kern<<<static_cast<unsigned>(l.sms * occ), kThreads, l.smem_dyn, s>>>(l.args);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename FT, int KW>
+cudaError_t mttkrp_batch_dispatch_typed(const BatchLaunch& l, cudaStream_t s) {
+#define ALTO_BLAUNCH_NR(NN, RR)                                                                  \
+  do {                                                                                           \
+    switch (l.variant) {                                                                         \
+      case kSmem: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kSmem>, l, s);          \
+      case kAtomic: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic>, l, s);      \
+      default: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg>, l, s);          \
+    }                                                                                            \
+  } while (0)
+#define ALTO_BLAUNCH_R(NN)              \
+  do {                                  \
+    switch (l.R) {                      \
+      case 8: ALTO_BLAUNCH_NR(NN, 8);   \
+      case 16: ALTO_BLAUNCH_NR(NN, 16); \
+      case 32: ALTO_BLAUNCH_NR(NN, 32); \
+      case 64: ALTO_BLAUNCH_NR(NN, 64); \
+      default: break;                   \
+    }                                   \
+  } while (0)
+  switch (l.N) {
+    case 2: ALTO_BLAUNCH_R(2); break;
+    case 3: ALTO_BLAUNCH_R(3); break;
+    case 4: ALTO_BLAUNCH_R(4); break;
+    case 5: ALTO_BLAUNCH_R(5); break;
+    default: break;
+  }
+#undef ALTO_BLAUNCH_R
+#undef ALTO_BLAUNCH_NR
+  return cudaErrorInvalidValue;  // the host only groups specialised shapes
+}
+
 inline cudaError_t mttkrp_dispatch(const MttkrpLaunch& l, alto_dtype fdtype, cudaStream_t s) {
   switch (fdtype) {
     case ALTO_F64: return l.KW == 1 ? mttkrp_dispatch_f64_k1(l, s) : mttkrp_dispatch_f64_k2(l, s);
@@ -649,7 +827,7 @@ inline cudaError_t mttkrp_dispatch(const MttkrpLaunch& l, alto_dtype fdtype, cud
 // than the work units), each striding over the units.
 template <typename Kern>
 cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, int64_t units, cudaStream_t s) {
-  if (smem > 48 * 1024) {
+  if (smem > 0) {  // the default limit is 48 KB minus the static shared memory
     const cudaError_t e =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;

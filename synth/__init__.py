@@ -2,8 +2,9 @@
 
 This package is shared by the tests, the benchmark, the oracle checks and
 the CUDA library's callers.  It holds none of ALTO's arithmetic: it only
-draws coordinates, values and factor matrices from seeded numpy generators
-and removes duplicate coordinates.
+draws coordinates, values and factor matrices from seeded generators (numpy
+for everything the oracle checks; torch's device generator for bulk timing
+data) and removes duplicate coordinates.
 
 Coordinate laws (stand-ins for the FROSTT / HaTen2 tensors of Table 1, which
 are not available here):
@@ -132,7 +133,7 @@ def _radix_fits(dims):
 
 def _linear(coords, dims):
     """Plain row-major linear index of each coordinate tuple (a dedup key)."""
-    key = torch.zeros(coords[0].shape[0], dtype=torch.int64)
+    key = torch.zeros(coords[0].shape[0], dtype=torch.int64, device=coords[0].device)
     for c, d in zip(coords, dims):
         key.mul_(int(d)).add_(c)
     return key
@@ -165,7 +166,7 @@ def _mix64(x):
 
 
 def _hash(coords):
-    h = torch.zeros(coords[0].shape[0], dtype=torch.int64)
+    h = torch.zeros(coords[0].shape[0], dtype=torch.int64, device=coords[0].device)
     for c in coords:
         h = _mix64(h ^ c)
     return h
@@ -175,7 +176,7 @@ def _sorted_unique(keys):
     s, _ = torch.sort(keys)
     if s.numel() == 0:
         return s
-    keep = torch.ones(s.numel(), dtype=torch.bool)
+    keep = torch.ones(s.numel(), dtype=torch.bool, device=s.device)
     keep[1:] = s[1:] != s[:-1]
     return s[keep]
 
@@ -184,7 +185,7 @@ def _first_unique(h):
     """Indices of the first occurrence of every distinct value of h."""
     order = torch.sort(h, stable=True)[1]
     s = h[order]
-    keep = torch.ones(s.numel(), dtype=torch.bool)
+    keep = torch.ones(s.numel(), dtype=torch.bool, device=s.device)
     keep[1:] = s[1:] != s[:-1]
     return order[keep]
 
@@ -305,3 +306,81 @@ def batch_config(seed):
         cfg["cluster_s"] = 1.2
         cfg["box"] = 64
     return cfg
+
+
+# ---------------------------------------------------------------------------
+# device-side generation (bulk timing data for variant selection)
+
+
+def tensor_torch(cfg, device="cuda"):
+    """The configuration's laws drawn with torch's generator on `device`
+    (fast bulk generation for variant timing; not the numpy stream, so not
+    for oracle parity).  Returns (dims, idx: list of int32 device tensors,
+    vals: float32 device tensor), nonzeros distinct and in random order."""
+    g = torch.Generator(device=device).manual_seed(int(cfg["seed"]))
+    dims = tuple(int(d) for d in cfg["dims"])
+    M = int(cfg["nnz"])
+    N = len(dims)
+    laws = cfg["laws"]
+
+    def zipf_sampler(I, s):
+        w = torch.arange(1, I + 1, dtype=torch.float64, device=device) ** (-float(s))
+        cdf = torch.cumsum(w, 0)
+        cdf /= cdf[-1].clone()
+        return lambda n: torch.searchsorted(cdf, torch.rand(n, generator=g, dtype=torch.float64, device=device),
+                                            right=True).clamp_(max=I - 1)
+
+    if laws and laws[0] == "clustered":
+        nc = int(cfg.get("clusters", 1024))
+        boxes = [min(int(cfg.get("box", 64)), d) for d in dims]
+        centres = [torch.randint(0, d - b + 1, (nc,), generator=g, device=device) for d, b in zip(dims, boxes)]
+        z = zipf_sampler(nc, cfg.get("cluster_s", 1.2))
+        cperm = torch.randperm(nc, generator=g, device=device)
+
+        def draw(n):
+            c = cperm[z(n)]
+            return [centres[m][c] + torch.randint(0, boxes[m], (n,), generator=g, device=device) for m in range(N)]
+    else:
+        samplers = []
+        for law, I in zip(laws, dims):
+            if law == "uniform":
+                samplers.append(lambda n, I=I: torch.randint(0, I, (n,), generator=g, device=device))
+            else:
+                zs = zipf_sampler(I, law[1])
+                perm = torch.randperm(I, generator=g, device=device)
+                samplers.append(lambda n, zs=zs, perm=perm: perm[zs(n)])
+
+        def draw(n):
+            return [smp(n) for smp in samplers]
+
+    batch = max(1024, int(M * 1.15))
+    if _radix_fits(dims):
+        keys = torch.zeros(0, dtype=torch.int64, device=device)
+        while keys.shape[0] < M:
+            need = M - keys.shape[0]
+            n = batch if keys.shape[0] == 0 else max(1024, int(need * 1.5))
+            keys = _sorted_unique(torch.cat([keys, _linear(draw(n), dims)]))
+        sel = torch.randperm(keys.shape[0], generator=g, device=device)[:M]
+        coords = _unlinear(keys[sel], dims)
+    else:
+        coords = [torch.zeros(0, dtype=torch.int64, device=device) for _ in range(N)]
+        h = torch.zeros(0, dtype=torch.int64, device=device)
+        while coords[0].shape[0] < M:
+            need = M - coords[0].shape[0]
+            n = batch if coords[0].shape[0] == 0 else max(1024, int(need * 1.5))
+            c = draw(n)
+            allc = [torch.cat([a, b]) for a, b in zip(coords, c)]
+            allh = torch.cat([h, _hash(c)])
+            first, _ = torch.sort(_first_unique(allh))
+            coords = [a[first] for a in allc]
+            h = allh[first]
+        sel = torch.randperm(coords[0].shape[0], generator=g, device=device)[:M]
+        coords = [a[sel] for a in coords]
+    vals = torch.rand(M, generator=g, device=device, dtype=torch.float32)
+    return dims, [c.to(torch.int32) for c in coords], vals
+
+
+def factors_torch(cfg, device="cuda", dtype=torch.float32, seed_offset=1000):
+    """N(0,1) factor matrices drawn on `device`."""
+    g = torch.Generator(device=device).manual_seed(int(cfg["seed"]) + seed_offset)
+    return [torch.randn(d, cfg["rank"], generator=g, device=device).to(dtype) for d in cfg["dims"]]
