@@ -69,7 +69,10 @@ typedef enum {
  *   key_bits : 0 = smallest native word that holds the index (64 or 128,
  *              Sec. 4.2.3); 64 or 128 forces a width (64 fails with
  *              ALTO_EOVERFLOW when the index needs more bits).
- *   nparts   : number L of equal-nnz line segments (Sec. 3.2); 0 = auto.
+ *   nparts   : number L of equal-nnz line segments (Sec. 3.2); 0 = auto:
+ *              segments of 2048 nonzeros, halved down to 256 while the
+ *              tensor gives fewer than two thread-block units (8 segments
+ *              each) per SM.
  *   variant  : per-mode MTTKRP variant (alto_variant); 0 = auto.
  *   use_flags: 1 = store boundary/internal helper flags in the unused key
  *              bits for modes whose fiber reuse is at most 4 (Sec. 3.3).
@@ -344,8 +347,11 @@ alto_status alto_linearize_noalloc(int nmodes, const uint64_t *dims,
  * output outs[i] (as for alto_mttkrp), using variants[i] (alto_variant, 0 =
  * automatic; NULL = all automatic).  Items of one kernel shape (order, key
  * width, rank, variant) run in one persistent launch over a device work list
- * of their thread-block units; items without a specialised kernel run on
- * their own; the device-memory Temp variant is replaced by warp aggregation.
+ * of their thread-block units; the launches sit on parallel branches of the
+ * graph (the costliest group first) so later groups fill the SMs that
+ * earlier ones release; items without a
+ * specialised kernel run on their own; the device-memory Temp variant is
+ * replaced by warp aggregation.
  * The graph captures the given pointers: later runs read the factors' and
  * write the outputs' current contents.  Capture happens on `stream` (on a
  * private stream when `stream` is the legacy default stream, which cannot

@@ -15,8 +15,22 @@ namespace {
 thread_local char g_err[512] = "";
 std::atomic<uint64_t> g_launches{0};
 
-// Default line-segment length (nonzeros per warp work unit).
-constexpr int64_t kSegNnz = 2048;
+constexpr int64_t kSegNnz = 2048;    // default nonzeros per line segment
+constexpr int64_t kMinSegNnz = 256;  // smallest automatic segment
+
+// Automatic L: segments of kSegNnz nonzeros, halved (down to kMinSegNnz)
+// while the tensor would give fewer than two thread-block units per SM, so
+// that small tensors still spread over the GPU.
+int64_t auto_segments(int64_t nnz) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  int64_t seg = kSegNnz;
+  const int64_t unit = alto::kUnitSegs;
+  while (seg > kMinSegNnz && (nnz + seg * unit - 1) / (seg * unit) < 2 * static_cast<int64_t>(sms)) seg >>= 1;
+  return (nnz + seg - 1) / seg;
+}
 
 }  // namespace
 
@@ -268,7 +282,7 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
       }
   }
   t->lay = lay;
-  t->L = nnz > 0 ? (o.nparts > 0 ? (o.nparts < nnz ? o.nparts : nnz) : (nnz + kSegNnz - 1) / kSegNnz) : 1;
+  t->L = nnz > 0 ? (o.nparts > 0 ? (o.nparts < nnz ? o.nparts : nnz) : auto_segments(nnz)) : 1;
 
   ALLOC(t->status, int*, sizeof(int) * 4);
   CK(cudaMemsetAsync(t->status, 0, sizeof(int) * 4, s));

@@ -4,6 +4,7 @@
 // device work list of its items' thread-block units, so small tensors share
 // the GPU instead of each occupying a launch.  Items whose shape has no
 // specialised kernel run on their own inside the same graph.
+#include <algorithm>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -35,6 +36,7 @@ namespace {
 
 constexpr int kBatchHotReplicas = 8;
 constexpr int kBatchHotCap = 256;
+constexpr size_t kBatchBranches = 16;  // parallel branches of the graph
 
 void free_plan(alto_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -72,6 +74,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
                                   ranks == nullptr || outs == nullptr)))
     return fail(ALTO_EINVAL, "bad batch arguments");
   const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
+  const size_t fsz = fdtype == ALTO_F64 ? 8 : (fdtype == ALTO_F32 ? 4 : 2);
   for (int i = 0; i < count; ++i) {
     if (tensors[i] == nullptr) return fail(ALTO_EINVAL, "item %d: null tensor", i);
     const int v = variants ? variants[i] : ALTO_VAR_AUTO;
@@ -85,27 +88,40 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
 
   // item descriptions, grouped by kernel shape
   using Key = std::tuple<int, int, int, int>;  // N, KW, R, variant
-  std::map<Key, std::vector<MttkrpArgs>> groups;
-  std::map<Key, size_t> group_smem;
-  std::vector<int> single;                        // items run on their own
-  std::vector<HotItem> hot_items;
-  std::vector<int64_t> hot_prefix(1, 0);
   struct Zero {
     void* p;
     size_t bytes;
   };
-  std::vector<Zero> zeros;
+  struct HostGroup {
+    std::vector<MttkrpArgs> items;
+    std::vector<Zero> zeros;  // outputs and hot-row replicas of the items
+    size_t smem = 0;
+    double cost = 0;          // estimated work: streamed and gathered bytes
+  };
+  std::map<Key, HostGroup> groups;
+  std::vector<int> single;    // items run on their own
+  std::vector<Zero> empty_zeros;
+  std::vector<HotItem> hot_items;
+  std::vector<int64_t> hot_prefix(1, 0);
   for (int i = 0; i < count; ++i) {
     alto_tensor_s* t = tensors[i];
     const int mode = modes[i], R = ranks[i];
-    zeros.push_back({outs[i], static_cast<size_t>(t->lay.dims[mode]) * R * osz});
-    if (t->M == 0) continue;
+    const Zero z{outs[i], static_cast<size_t>(t->lay.dims[mode]) * R * osz};
+    if (t->M == 0) {
+      empty_zeros.push_back(z);
+      continue;
+    }
     int v = resolve_variant(t, mode, R, osz, variants ? variants[i] : ALTO_VAR_AUTO);
     if (v == ALTO_VAR_TEMP) v = ALTO_VAR_WARPAGG;  // the per-unit device Temp is not batched
     if (!mttkrp_specialised(t->lay.N, R)) {
       single.push_back(i);
       continue;
     }
+    const Key key{t->lay.N, t->lay.KW, R, v};
+    HostGroup& hg = groups[key];
+    hg.zeros.push_back(z);
+    hg.cost += static_cast<double>(t->M) * (8.0 * t->lay.KW + 4.0 + (t->lay.N - 1) * R * fsz) +
+               static_cast<double>(z.bytes);
     MttkrpLaunch l{};
     fill_launch(t, mode, factors[i], R, outs[i], &l);
     size_t smem = 0;
@@ -123,7 +139,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
       e = cudaMalloc(&rep, bytes);
       if (e != cudaSuccess) break;
       b->bufs.push_back(rep);
-      zeros.push_back({rep, bytes});
+      hg.zeros.push_back({rep, bytes});
       l.args.hot = t->hot[mode];
       l.args.hot_n = H;
       l.args.hot_bits = bits;
@@ -133,30 +149,32 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
       hot_items.push_back({rep, t->hot[mode], outs[i], H, R, kBatchHotReplicas, 0});
       hot_prefix.push_back(hot_prefix.back() + static_cast<int64_t>(H) * R);
     }
-    const Key key{t->lay.N, t->lay.KW, R, v};
-    groups[key].push_back(l.args);
-    group_smem[key] = std::max(group_smem[key], smem);
+    hg.items.push_back(l.args);
+    hg.smem = std::max(hg.smem, smem);
   }
 
-  // device work lists
+  // device work lists, largest group first
   struct Group {
     Key key;
+    const HostGroup* host;
     MttkrpArgs* items;
     int64_t* prefix;
-    int n;
+    int64_t units;
   };
   std::vector<Group> dev_groups;
   if (e == cudaSuccess) {
     for (auto& kv : groups) {
       std::vector<int64_t> prefix(1, 0);
-      for (const MttkrpArgs& a : kv.second) prefix.push_back(prefix.back() + (a.L + kUnitSegs - 1) / kUnitSegs);
-      Group g{kv.first, nullptr, nullptr, static_cast<int>(kv.second.size())};
-      g.items = upload(b, kv.second, &e);
+      for (const MttkrpArgs& a : kv.second.items) prefix.push_back(prefix.back() + (a.L + kUnitSegs - 1) / kUnitSegs);
+      Group g{kv.first, &kv.second, nullptr, nullptr, prefix.back()};
+      g.items = upload(b, kv.second.items, &e);
       if (e != cudaSuccess) break;
       g.prefix = upload(b, prefix, &e);
       if (e != cudaSuccess) break;
       dev_groups.push_back(g);
     }
+    std::sort(dev_groups.begin(), dev_groups.end(),
+              [](const Group& x, const Group& y) { return x.host->cost > y.host->cost; });
   }
   HotItem* d_hot = nullptr;
   int64_t* d_hot_prefix = nullptr;
@@ -170,38 +188,65 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     return fail(ALTO_ECUDA, "batch plan: %s", cudaGetErrorString(e));
   }
 
-  // capture every launch into one graph
+  // Capture: the groups (their zeroing, then their persistent launch, the
+  // costliest first) and the stand-alone items run on parallel branches of
+  // the graph; the hot-row reduction follows once every branch is done.
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // the legacy default stream cannot be captured: use a private stream
-  cudaStream_t own = nullptr;
+  const int branches = static_cast<int>(std::min<size_t>(kBatchBranches, dev_groups.size() + single.size()));
+  std::vector<cudaStream_t> fs(branches, nullptr);
+  std::vector<cudaEvent_t> join(branches, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaStream_t own = nullptr;  // the legacy default stream cannot be captured
   if (s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) {
     e = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      free_plan(b);
-      delete b;
-      return fail(ALTO_ECUDA, "batch capture stream: %s", cudaGetErrorString(e));
-    }
     s = own;
   }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int k = 0; e == cudaSuccess && k < branches; ++k) {
+    e = cudaStreamCreateWithFlags(&fs[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming);
+  }
   const uint64_t launches0 = launch_total();
-  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-  for (size_t z = 0; e == cudaSuccess && z < zeros.size(); ++z) e = cudaMemsetAsync(zeros[z].p, 0, zeros[z].bytes, s);
+  bool capturing = false;
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    capturing = e == cudaSuccess;
+  }
+  for (size_t z = 0; e == cudaSuccess && z < empty_zeros.size(); ++z)
+    e = cudaMemsetAsync(empty_zeros[z].p, 0, empty_zeros[z].bytes, s);
+  if (e == cudaSuccess && branches > 0) e = cudaEventRecord(fork, s);
+  for (int k = 0; e == cudaSuccess && k < branches; ++k) e = cudaStreamWaitEvent(fs[k], fork, 0);
   for (size_t gi = 0; e == cudaSuccess && gi < dev_groups.size(); ++gi) {
     const Group& g = dev_groups[gi];
+    cudaStream_t bs = fs[gi % branches];
+    for (size_t z = 0; e == cudaSuccess && z < g.host->zeros.size(); ++z)
+      e = cudaMemsetAsync(g.host->zeros[z].p, 0, g.host->zeros[z].bytes, bs);
+    if (e != cudaSuccess) break;
     BatchLaunch bl{};
     bl.args.items = g.items;
     bl.args.unit_prefix = g.prefix;
-    bl.args.nitems = g.n;
+    bl.args.nitems = static_cast<int>(g.host->items.size());
     bl.args.hot_replicas = kBatchHotReplicas;
     bl.N = std::get<0>(g.key);
     bl.KW = std::get<1>(g.key);
     bl.R = std::get<2>(g.key);
     bl.variant = std::get<3>(g.key);
     bl.sms = sms;
-    bl.smem_dyn = group_smem[g.key];
-    e = mttkrp_batch_dispatch(bl, fdtype, s);
+    bl.smem_dyn = g.host->smem;
+    bl.units = g.units;
+    e = mttkrp_batch_dispatch(bl, fdtype, bs);
+  }
+  for (size_t k = 0; e == cudaSuccess && k < single.size(); ++k) {
+    const int i = single[k];
+    // no specialised kernel: the generic one (which ignores the variant)
+    e = mttkrp_launch(tensors[i], modes[i], factors[i], ranks[i], fdtype, outs[i], ALTO_VAR_ATOMIC, osz,
+                      fs[(dev_groups.size() + k) % branches]);
+  }
+  for (int k = 0; e == cudaSuccess && k < branches; ++k) {
+    e = cudaEventRecord(join[k], fs[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join[k], 0);
   }
   if (e == cudaSuccess && !hot_items.empty()) {
     const int64_t tot = hot_prefix.back();
@@ -216,24 +261,26 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     note_launch();
     e = cudaGetLastError();
   }
-  for (size_t k = 0; e == cudaSuccess && k < single.size(); ++k) {
-    const int i = single[k];
-    // no specialised kernel: the generic one (which ignores the variant)
-    e = mttkrp_launch(tensors[i], modes[i], factors[i], ranks[i], fdtype, outs[i], ALTO_VAR_ATOMIC, osz, s);
-  }
   cudaGraph_t graph = nullptr;
-  const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (capturing) {
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
   // kernels captured, not launched: counted at every alto_batch_run instead
   const int kernels = static_cast<int>(launch_total() - launches0);
   note_launch(-kernels);
-  if (own != nullptr) cudaStreamDestroy(own);
-  if (e == cudaSuccess) e = e2;
   if (e == cudaSuccess) {
     b->graph = graph;
     e = cudaGraphInstantiate(&b->exec, graph, 0);
   } else if (graph) {
     cudaGraphDestroy(graph);
   }
+  for (int k = 0; k < branches; ++k) {
+    if (join[k]) cudaEventDestroy(join[k]);
+    if (fs[k]) cudaStreamDestroy(fs[k]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (own) cudaStreamDestroy(own);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_plan(b);

@@ -160,6 +160,7 @@ cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dt
 // Hot rows: every kHotSample-th nonzero is counted per row during the
 // segment statistics pass; the rows with the largest sampled counts (at most
 // kHotCap per mode) become the mode's hot list.
+constexpr int kUnitSegs = 8;  // line segments per MTTKRP thread-block unit
 constexpr int kHotSample = 16;
 constexpr int kHotCap = 1024;
 cudaError_t launch_segment_stats(const Layout& lay, const uint64_t* keys, int64_t M, int64_t L,

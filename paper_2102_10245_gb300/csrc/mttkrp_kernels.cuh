@@ -42,26 +42,34 @@ namespace alto {
 enum Policy { kAtomic = ALTO_VAR_ATOMIC, kWarpAgg = ALTO_VAR_WARPAGG, kSmem = ALTO_VAR_SMEM, kTemp = ALTO_VAR_TEMP };
 
 // ---------------------------------------------------------------------------
-// factor element traits: 16-byte loads of VEC elements, accumulation type AT
+// factor element traits: 16-byte loads of VEC elements, accumulation type AT;
+// gathered rows are held as RT words of PACK elements each (BF16 rows stay
+// packed in registers and are widened where they are used)
 template <typename FT>
 struct FTraits;
 template <>
 struct FTraits<float> {
   static constexpr int VEC = 4;
+  static constexpr int PACK = 1;
   using AT = float;
   using VT = float;
+  using RT = float;
 };
 template <>
 struct FTraits<double> {
   static constexpr int VEC = 2;
+  static constexpr int PACK = 1;
   using AT = double;
   using VT = double;
+  using RT = double;
 };
 template <>
 struct FTraits<__nv_bfloat16> {
   static constexpr int VEC = 8;
+  static constexpr int PACK = 2;
   using AT = float;
   using VT = float;
+  using RT = uint32_t;
 };
 
 // Column layout of one nonzero's row across its lane group: lane c of the
@@ -80,7 +88,7 @@ struct Cols {
 };
 
 template <typename FT>
-__device__ __forceinline__ void load16(const FT* p, typename FTraits<FT>::AT* v);
+__device__ __forceinline__ void load16(const FT* p, typename FTraits<FT>::RT* v);
 
 template <>
 __device__ __forceinline__ void load16<float>(const float* p, float* v) {
@@ -99,17 +107,18 @@ __device__ __forceinline__ void load16<double>(const double* p, double* v) {
 }
 
 template <>
-__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, uint32_t* v) {
   const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
-  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    __nv_bfloat162 h;
-    memcpy(&h, &w[j], 4);
-    const float2 f = __bfloat1622float2(h);
-    v[2 * j] = f.x;
-    v[2 * j + 1] = f.y;
-  }
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+
+// two BF16 values packed in a word (element 0 in the low half) as FP32: a
+// BF16 value is the upper 16 bits of the FP32 value with the same bits
+__device__ __forceinline__ float2 widen_bf16x2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
 // elementwise helpers, packed FP32x2 where the accumulation type is float
@@ -121,6 +130,34 @@ __device__ __forceinline__ void scale_into(float* t, float v, const float* a) {
     const float2 r = __fmul2_rn(v2, make_float2(a[e], a[e + 1]));
     t[e] = r.x;
     t[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void scale_into(float* t, float v, const uint32_t* a) {
+  const float2 v2 = make_float2(v, v);
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r = __fmul2_rn(v2, widen_bf16x2(a[e / 2]));
+    t[e] = r.x;
+    t[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void mul_into(float* t, const uint32_t* a) {
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r = __fmul2_rn(make_float2(t[e], t[e + 1]), widen_bf16x2(a[e / 2]));
+    t[e] = r.x;
+    t[e + 1] = r.y;
+  }
+}
+template <int K>
+__device__ __forceinline__ void fma_into(float* acc, const float* t, const uint32_t* a) {
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    const float2 r = __ffma2_rn(make_float2(t[e], t[e + 1]), widen_bf16x2(a[e / 2]), make_float2(acc[e], acc[e + 1]));
+    acc[e] = r.x;
+    acc[e + 1] = r.y;
   }
 }
 template <int K>
@@ -214,7 +251,6 @@ __device__ __forceinline__ int hot_lookup(const uint32_t* keys, const uint32_t* 
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr int kUnitSegs = 8;  // segments per thread-block unit
 static_assert(sizeof(MttkrpArgs) % 4 == 0, "MttkrpArgs is copied as 32-bit words");
 
 // staged tuple: N indices and the value, padded to 16-byte words
@@ -260,10 +296,10 @@ __device__ __forceinline__ Pos<N, VT> stage_load(const uint4* slot) {
   return p;
 }
 
-// gathered input rows of one position: (N-1) x CPL values
+// gathered input rows of one position: (N-1) x CPL values in RT words
 template <int N, int R, typename FT>
 struct Rows {
-  typename FTraits<FT>::AT u[N > 1 ? N - 1 : 1][Cols<R, FT>::CPL];
+  typename FTraits<FT>::RT u[N > 1 ? N - 1 : 1][Cols<R, FT>::CPL / FTraits<FT>::PACK];
 };
 
 template <int N, int R, typename FT, typename VT>
@@ -273,7 +309,7 @@ __device__ __forceinline__ void gather(const MttkrpArgs& a, const Pos<N, VT>& p,
   for (int s = 0; s < N - 1; ++s) {
     const FT* row = static_cast<const FT*>(a.f[s]) + static_cast<size_t>(p.id[s]) * R + c * C::VEC;
 #pragma unroll
-    for (int q = 0; q < C::PAIRS; ++q) load16<FT>(row + q * C::STRIDE, &r.u[s][q * C::VEC]);
+    for (int q = 0; q < C::PAIRS; ++q) load16<FT>(row + q * C::STRIDE, &r.u[s][q * C::VEC / FTraits<FT>::PACK]);
   }
 }
 
@@ -748,6 +784,7 @@ struct BatchLaunch {
   int variant;   // ATOMIC / WARPAGG / SMEM
   int sms;
   size_t smem_dyn;
+  int64_t units;  // thread-block units of all items
 };
 
 cudaError_t mttkrp_batch_dispatch_f32_k1(const BatchLaunch& l, cudaStream_t s);
@@ -778,7 +815,12 @@ cudaError_t launch_batch(Kern kern, const BatchLaunch& l, cudaStream_t s) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, l.smem_dyn);
   if (e != cudaSuccess) return e;
   if (occ < 1) occ = 1;
-  kern<<<static_cast<unsigned>(l.sms * occ), kThreads, l.smem_dyn, s>>>(l.args);
+  // every group may fill the device; groups on parallel graph branches take
+  // over the SMs that earlier groups' blocks release
+  int64_t g = static_cast<int64_t>(l.sms) * occ;
+  if (g > l.units) g = l.units;
+  if (g < 1) g = 1;
+  kern<<<static_cast<unsigned>(g), kThreads, l.smem_dyn, s>>>(l.args);
   note_launch();
   return cudaGetLastError();
 }
