@@ -251,6 +251,10 @@ __device__ __forceinline__ int hot_lookup(const uint32_t* keys, const uint32_t* 
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
+// Positions whose factor-row gathers are in flight ahead of the sum.  Depths 2
+// and 3 (with the register budget they need) measured no faster on GB300:
+// the L1 data path, not the latency of single gathers, bounds the kernel.
+constexpr int kGatherDepth = 1;
 static_assert(sizeof(MttkrpArgs) % 4 == 0, "MttkrpArgs is copied as 32-bit words");
 
 // staged tuple: N indices and the value, padded to 16-byte words
@@ -521,14 +525,21 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
     if (ok) stage_store<N, VT>(s_stage[warp][pos], id, v);
     __syncwarp();
 
-    // group g: positions g*PER .. g*PER + PER - 1, gathers one position
-    // ahead.  Loads past the chunk's end read its last valid slot again
-    // (harmless, the result is not used), so every load is unconditional
-    // and the pipeline registers rename instead of being copied.
+    // group g: positions g*PER .. g*PER + PER - 1, with the gathers of the
+    // next kGatherDepth positions in flight.  Loads past the chunk's end read
+    // its last valid slot again (harmless, the result is not used), so every
+    // load is unconditional and the pipeline registers rename instead of
+    // being copied.
     const int p0 = g * PER;
-    Pos<N, VT> cur = stage_load<N, VT>(s_stage[warp][p0 < cnt ? p0 : cnt - 1]);
-    Rows<N, R, FT> rc;
-    gather<N, R, FT>(a, cur, c, rc);
+    constexpr int D = PER < kGatherDepth ? PER : kGatherDepth;
+    Pos<N, VT> q[D + 1];        // q[0]: the position being summed; q[1..D]: gathers in flight
+    Rows<N, R, FT> rw[D + 1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int p = p0 + i;
+      q[i] = stage_load<N, VT>(s_stage[warp][p < cnt ? p : cnt - 1]);
+      gather<N, R, FT>(a, q[i], c, rw[i]);
+    }
     AT acc[K];
 #pragma unroll
     for (int e = 0; e < K; ++e) acc[e] = AT(0);
@@ -537,21 +548,21 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
       const int p = p0 + j;
       const bool has = p < cnt;
       const bool hasn = (j + 1 < PER) && (p + 1 < cnt);
-      Pos<N, VT> nxt;
-      Rows<N, R, FT> rn;
-      if (j + 1 < PER) {
-        nxt = stage_load<N, VT>(s_stage[warp][p + 1 < cnt ? p + 1 : cnt - 1]);
-        gather<N, R, FT>(a, nxt, c, rn);
+      if (j + D < PER) {
+        const int pn = p + D;
+        q[D] = stage_load<N, VT>(s_stage[warp][pn < cnt ? pn : cnt - 1]);
+        gather<N, R, FT>(a, q[D], c, rw[D]);
       }
+      const Pos<N, VT>& cur = q[0];
       if (has) {
         const uint32_t row = cur.id[N - 1];
         if constexpr (POL == kAtomic) {
           AT t[K];
-          product<N, R, FT>(cur, rc, t);
+          product<N, R, FT>(cur, rw[0], t);
           flush_global<R, FT>(out + static_cast<size_t>(row) * R, c, t);
         } else {
-          accumulate<N, R, FT>(cur, rc, acc);
-          if (!hasn || nxt.id[N - 1] != row) {
+          accumulate<N, R, FT>(cur, rw[0], acc);
+          if (!hasn || q[1].id[N - 1] != row) {
             if constexpr (POL == kSmem) {
               if (use_smem) {
                 flush_shared<R, FT>(dst + static_cast<size_t>(row - lo) * R, c, acc);
@@ -576,9 +587,11 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
           }
         }
       }
-      if (j + 1 < PER) {
-        cur = nxt;
-        rc = rn;
+      // advance the pipeline (register renames once unrolled)
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        q[i] = q[i + 1];
+        rw[i] = rw[i + 1];
       }
     }
     __syncwarp();
@@ -609,7 +622,7 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
 
 // One MTTKRP: persistent blocks stride over the units.
 template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads, 5) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
@@ -635,7 +648,7 @@ struct BatchArgs {
 };
 
 template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads, 5) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, 4) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
