@@ -189,6 +189,34 @@ class Predictor:
     def pick(self, feats):
         return self.scores(feats).argmin(axis=1)
 
+    def configure(self, at, rank, fdtype=BF16):
+        """Set every mode of ``at`` to the predicted variant (alto_set_variant),
+        so plain alto_mttkrp / alto_cpals calls use it; returns the variants."""
+        feats = np.array([features(at, n, rank, fdtype) for n in range(at.N)])
+        picks = [VARIANTS[int(p)] for p in self.pick(feats)]
+        for n, v in enumerate(picks):
+            at.set_variant(n, v)
+        return picks
+
+    def save(self, path):
+        arrays = {"mu": self.mu, "sd": self.sd, "hidden": np.array(self.hidden)}
+        for i, (W, b) in enumerate(self.net.params):
+            arrays["W%d" % i] = W.cpu().numpy()
+            arrays["b%d" % i] = b.cpu().numpy()
+        np.savez(path, **arrays)
+
+    @classmethod
+    def load(cls, path, device="cuda"):
+        d = np.load(path)
+        p = cls(hidden=tuple(int(h) for h in d["hidden"]), device=device)
+        p.mu, p.sd = d["mu"], d["sd"]
+        sizes = [d["W0"].shape[1]] + [d["W%d" % i].shape[0] for i in range(len(p.hidden) + 1)]
+        p.net = MLP(sizes, device=device)
+        for i, pr in enumerate(p.net.params):
+            pr[0].copy_(torch.from_numpy(d["W%d" % i]))
+            pr[1].copy_(torch.from_numpy(d["b%d" % i]))
+        return p
+
     def choose(self, feats, measure=None, margin=0.0):
         """Picks with the autotuner as fallback: rows whose two best
         predictions are within ``margin`` (log2 units) are timed by

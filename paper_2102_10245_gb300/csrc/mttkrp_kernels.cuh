@@ -35,6 +35,8 @@
 // All policies compute the same sums; only the rounding order differs.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace alto {
@@ -317,13 +319,53 @@ __device__ __forceinline__ void gather(const MttkrpArgs& a, const Pos<N, VT>& p,
   }
 }
 
+// Exact FP32 products of two packed BF16 pairs (an 8-bit by 8-bit significand
+// product fits FP32's 24 bits), by the mixed-precision FMA with a zero addend.
+__device__ __forceinline__ float2 bf16x2_mul_exact(uint32_t a, uint32_t b) {
+  float lo, hi;
+  asm("{\n\t.reg .b16 al, ah, bl, bh;\n\t"
+      "mov.b32 {al, ah}, %2;\n\t"
+      "mov.b32 {bl, bh}, %3;\n\t"
+      "fma.rn.f32.bf16 %0, al, bl, 0f00000000;\n\t"
+      "fma.rn.f32.bf16 %1, ah, bh, 0f00000000;\n\t}"
+      : "=f"(lo), "=f"(hi)
+      : "r"(a), "r"(b));
+  return make_float2(lo, hi);
+}
+
+// BF16 rows: the first two rows' product is formed exactly from the packed
+// words, the other rows are widened and multiplied in FP32, and the value
+// scales last: pr = u_0 * u_1 * ... * u_{N-2} (FP32), so that
+// t = v * pr and acc += v * pr are single packed FP32 operations.
+template <int N, int R>
+__device__ __forceinline__ void bf16_row_product(const Rows<N, R, __nv_bfloat16>& r, float* pr) {
+  constexpr int K = Cols<R, __nv_bfloat16>::CPL;
+#pragma unroll
+  for (int e = 0; e < K; e += 2) {
+    float2 x = bf16x2_mul_exact(r.u[0][e / 2], r.u[1][e / 2]);
+#pragma unroll
+    for (int s = 2; s < N - 1; ++s) x = __fmul2_rn(x, widen_bf16x2(r.u[s][e / 2]));
+    pr[e] = x.x;
+    pr[e + 1] = x.y;
+  }
+}
+
 // t = v * prod_s u_s
 template <int N, int R, typename FT, typename VT>
 __device__ __forceinline__ void product(const Pos<N, VT>& p, const Rows<N, R, FT>& r,
                                         typename FTraits<FT>::AT* t) {
   using AT = typename FTraits<FT>::AT;
   constexpr int K = Cols<R, FT>::CPL;
-  if constexpr (N == 1) {
+  if constexpr (std::is_same_v<FT, __nv_bfloat16> && N >= 3) {
+    bf16_row_product<N, R>(r, t);
+    const float2 v2 = make_float2(static_cast<float>(p.v), static_cast<float>(p.v));
+#pragma unroll
+    for (int e = 0; e < K; e += 2) {
+      const float2 x = __fmul2_rn(v2, make_float2(t[e], t[e + 1]));
+      t[e] = x.x;
+      t[e + 1] = x.y;
+    }
+  } else if constexpr (N == 1) {
 #pragma unroll
     for (int e = 0; e < K; ++e) t[e] = static_cast<AT>(p.v);
   } else {
@@ -340,7 +382,16 @@ __device__ __forceinline__ void accumulate(const Pos<N, VT>& p, const Rows<N, R,
   using AT = typename FTraits<FT>::AT;
   constexpr int K = Cols<R, FT>::CPL;
   AT t[K];
-  if constexpr (N <= 2) {
+  if constexpr (std::is_same_v<FT, __nv_bfloat16> && N >= 3) {
+    bf16_row_product<N, R>(r, t);
+    const float2 v2 = make_float2(static_cast<float>(p.v), static_cast<float>(p.v));
+#pragma unroll
+    for (int e = 0; e < K; e += 2) {
+      const float2 x = __ffma2_rn(v2, make_float2(t[e], t[e + 1]), make_float2(acc[e], acc[e + 1]));
+      acc[e] = x.x;
+      acc[e + 1] = x.y;
+    }
+  } else if constexpr (N <= 2) {
     product<N, R, FT>(p, r, t);
 #pragma unroll
     for (int e = 0; e < K; ++e) acc[e] += t[e];

@@ -94,3 +94,20 @@ def test_collect_small(alto_lib):
     assert d["features"].shape == (rows, len(tune.FEATURES)) and d["times"].shape == (rows, len(tune.VARIANTS))
     assert (d["times"] > 0).all() and list(d["meta"][:, 0]) == [3] * len(synth.batch_config(3)["dims"]) + \
         [4] * len(synth.batch_config(4)["dims"])
+
+
+def test_configure_save_load(trained, tmp_path):
+    from paper_2102_10245_gb300 import autotune as tune
+    pred, d, _ = trained
+    f = d["heldout_features"][:64]
+    path = str(tmp_path / "pred.npz")
+    pred.save(path)
+    again = tune.Predictor.load(path)
+    assert np.array_equal(again.pick(f), pred.pick(f))
+    cfg = synth.batch_config(11)
+    cfg["dims"] = tuple(min(x, 100_000) for x in cfg["dims"])
+    cfg["nnz"] = min(cfg["nnz"], 100_000)
+    at, factors = tune.make_item(cfg)
+    picks = again.configure(at, cfg["rank"])
+    assert at.stats()["variant"] == picks
+    at.close()
