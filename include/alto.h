@@ -51,7 +51,8 @@ typedef enum {
 
 /* Output-accumulation variants of MTTKRP (Alg. 2 and Sec. 3.3). */
 typedef enum {
-    ALTO_VAR_AUTO = 0,    /* the library's choice (Sec. 3.3 reuse rule) */
+    ALTO_VAR_AUTO = 0,    /* the library's choice (Sec. 3.3 reuse rule:
+                             reuse <= 4 -> ATOMIC, else WARPAGG) */
     ALTO_VAR_ATOMIC = 1,  /* direct atomic update per nonzero (Alg. 2, ATOMIC) */
     ALTO_VAR_WARPAGG = 2, /* warp-level pre-aggregation of equal output rows,
                              then atomics */
@@ -260,9 +261,8 @@ alto_status alto_set_variant(alto_t t, int mode, int variant);
 /* alto_resolve_variant -- the accumulation variant an alto_mttkrp call of
  * this mode, rank and factor dtype runs when it asks for `variant`
  * (ALTO_VAR_AUTO: the per-mode override, else the reuse rule of Sec. 3.3
- * adapted to the GPU: reuse M/I_n <= 4 -> ATOMIC; else SMEM when 9 in 10
- * thread-block units' output intervals fit the shared buffer; else
- * WARPAGG).  Shapes without a specialised kernel report ATOMIC (the generic
+ * adapted to the GPU: reuse M/I_n <= 4 -> ATOMIC, else WARPAGG; SMEM is
+ * never chosen automatically).  Shapes without a specialised kernel report ATOMIC (the generic
  * kernel).  *out receives one of ALTO_VAR_ATOMIC..ALTO_VAR_TEMP.  Host-only. */
 alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_dtype fdtype, int variant, int *out);
 

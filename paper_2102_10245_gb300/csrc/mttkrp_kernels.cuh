@@ -10,7 +10,7 @@
 //      being fetched;
 //   2. the decoded tuple (N indices + value) is staged in shared memory;
 //   3. groups of LPN lanes own one staged nonzero at a time, each lane CPL
-//      columns in 16-byte pieces; the gathers of the next position are
+//      columns in VEC-element pieces; the gathers of the next position are
 //      issued before the current position's arithmetic (Hadamard product of
 //      the N-1 input rows, scaled by the value, packed FP32x2 math).
 //
@@ -44,9 +44,11 @@ namespace alto {
 enum Policy { kAtomic = ALTO_VAR_ATOMIC, kWarpAgg = ALTO_VAR_WARPAGG, kSmem = ALTO_VAR_SMEM, kTemp = ALTO_VAR_TEMP };
 
 // ---------------------------------------------------------------------------
-// factor element traits: 16-byte loads of VEC elements, accumulation type AT;
-// gathered rows are held as RT words of PACK elements each (BF16 rows stay
-// packed in registers and are widened where they are used)
+// factor element traits: loads of VEC elements per lane, accumulation type
+// AT; gathered rows are held as RT words of PACK elements each (BF16 rows
+// stay packed in registers and are widened where they are used).  BF16 rows
+// are loaded 8 bytes per lane: with 16-byte loads a warp instruction touched
+// twice as many rows and the kernel ran 1.6x slower on GB300.
 template <typename FT>
 struct FTraits;
 template <>
@@ -67,7 +69,7 @@ struct FTraits<double> {
 };
 template <>
 struct FTraits<__nv_bfloat16> {
-  static constexpr int VEC = 8;
+  static constexpr int VEC = 4;
   static constexpr int PACK = 2;
   using AT = float;
   using VT = float;
@@ -75,8 +77,8 @@ struct FTraits<__nv_bfloat16> {
 };
 
 // Column layout of one nonzero's row across its lane group: lane c of the
-// group owns the 16-byte pieces at columns c*VEC + q*STRIDE, q < PAIRS.  One
-// piece per lane up to 32 lanes keeps every warp-wide access at one L1
+// group owns the VEC-element pieces at columns c*VEC + q*STRIDE, q < PAIRS.
+// One piece per lane up to 32 lanes keeps every warp-wide access at one L1
 // wavefront per row (the SM's L1 / shared path moves about 128 bytes per
 // clock, which bounds the gathers).
 template <int R, typename FT>
@@ -90,10 +92,10 @@ struct Cols {
 };
 
 template <typename FT>
-__device__ __forceinline__ void load16(const FT* p, typename FTraits<FT>::RT* v);
+__device__ __forceinline__ void load_vec(const FT* p, typename FTraits<FT>::RT* v);
 
 template <>
-__device__ __forceinline__ void load16<float>(const float* p, float* v) {
+__device__ __forceinline__ void load_vec<float>(const float* p, float* v) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
   v[0] = a.x;
   v[1] = a.y;
@@ -102,19 +104,17 @@ __device__ __forceinline__ void load16<float>(const float* p, float* v) {
 }
 
 template <>
-__device__ __forceinline__ void load16<double>(const double* p, double* v) {
+__device__ __forceinline__ void load_vec<double>(const double* p, double* v) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(p));
   v[0] = a.x;
   v[1] = a.y;
 }
 
 template <>
-__device__ __forceinline__ void load16<__nv_bfloat16>(const __nv_bfloat16* p, uint32_t* v) {
-  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+__device__ __forceinline__ void load_vec<__nv_bfloat16>(const __nv_bfloat16* p, uint32_t* v) {
+  const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
   v[0] = a.x;
   v[1] = a.y;
-  v[2] = a.z;
-  v[3] = a.w;
 }
 
 // two BF16 values packed in a word (element 0 in the low half) as FP32: a
@@ -200,6 +200,7 @@ __device__ __forceinline__ void fma_into(double* acc, const double* t, const dou
 // VEC accumulators into global memory with vector atomics
 template <int VEC>
 __device__ __forceinline__ void red_vec(float* out, const float* v) {
+  static_assert(VEC % 4 == 0, "FP32 accumulators flush in fours");
 #pragma unroll
   for (int j = 0; j < VEC; j += 4) red_add_v4(out + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
 }
@@ -315,7 +316,7 @@ __device__ __forceinline__ void gather(const MttkrpArgs& a, const Pos<N, VT>& p,
   for (int s = 0; s < N - 1; ++s) {
     const FT* row = static_cast<const FT*>(a.f[s]) + static_cast<size_t>(p.id[s]) * R + c * C::VEC;
 #pragma unroll
-    for (int q = 0; q < C::PAIRS; ++q) load16<FT>(row + q * C::STRIDE, &r.u[s][q * C::VEC / FTraits<FT>::PACK]);
+    for (int q = 0; q < C::PAIRS; ++q) load_vec<FT>(row + q * C::STRIDE, &r.u[s][q * C::VEC / FTraits<FT>::PACK]);
   }
 }
 
