@@ -94,3 +94,29 @@ def test_singular_gram_reports_not_spd():
     # the handle and the context stay usable
     lam, fits = at.cpals([dev(u.copy()) for u in synth.factors(cfg)], 1)
     assert np.isfinite(fits[0])
+
+
+@pytest.mark.parametrize("R", [8, 24, 64])
+@pytest.mark.parametrize("fdt", ["f64", "f32"])
+def test_ranks_match_oracle(R, fdt):
+    """Every update path: the fused one-pass update (R <= 32), the two-pass
+    warp-row update (R = 64) and the generic one (other ranks)."""
+    rng = np.random.default_rng(R)
+    dims = (300, 200, 150)
+    M = 20_000
+    idx = [rng.integers(0, d, M).astype(np.uint32) for d in dims]
+    vals = rng.random(M).astype(np.float64 if fdt == "f64" else np.float32)
+    U0 = [rng.random((d, R)) for d in dims]
+    at = make(dims, idx, vals)
+    npdt = np.float64 if fdt == "f64" else np.float32
+    Ud = [dev(u.astype(npdt)) for u in U0]
+    iters = 4
+    lam, fits = at.cpals(Ud, iters)
+    U, lam_o, fits_o, _ = oracle.cpals(dims, idx, vals.astype(np.float64),
+                                       [u.astype(npdt).astype(np.float64) for u in U0], iters)
+    tol = 1e-9 if fdt == "f64" else 1e-3
+    print(R, fdt, "fits gpu", fits, "oracle", fits_o)
+    assert np.allclose(fits, fits_o, rtol=0, atol=tol * 10)
+    assert rel_err(lam.cpu().numpy(), lam_o) <= tol
+    for n in range(3):
+        assert rel_err(Ud[n].cpu().numpy(), U[n]) <= tol
