@@ -262,8 +262,10 @@ alto_status alto_set_variant(alto_t t, int mode, int variant);
  * this mode, rank and factor dtype runs when it asks for `variant`
  * (ALTO_VAR_AUTO: the per-mode override, else the reuse rule of Sec. 3.3
  * adapted to the GPU: reuse M/I_n <= 4 -> ATOMIC, else WARPAGG; SMEM is
- * never chosen automatically).  Shapes without a specialised kernel report ATOMIC (the generic
- * kernel).  *out receives one of ALTO_VAR_ATOMIC..ALTO_VAR_TEMP.  Host-only. */
+ * never chosen automatically).  Shapes without a specialised kernel report
+ * ATOMIC (the generic kernel).  *out receives one of
+ * ALTO_VAR_ATOMIC..ALTO_VAR_TEMP.  Host-only.  Errors: ALTO_EINVAL for a
+ * NULL handle or output, a bad mode, rank, dtype or variant. */
 alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_dtype fdtype, int variant, int *out);
 
 /* alto_check -- synchronise `stream` and report a recorded device error. */
@@ -308,7 +310,8 @@ alto_status alto_profile(alto_t t, int enable);
 alto_status alto_profile_read(alto_t t, double *ms, int64_t *calls);
 
 /* alto_launch_count -- number of kernels the library has launched in this
- * process so far (all handles). */
+ * process so far (all handles); the kernels of an alto_batch_run graph count
+ * at every run. */
 alto_status alto_launch_count(uint64_t *count);
 
 /*
