@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--nparts", default="0", help="line segments L (0 = automatic); --mttkrp-only: comma list")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-bf16", action="store_true", help="skip the BF16-factor CP-ALS comparison")
     p.add_argument("--nnz", type=int, default=0,
                    help="profiling only: the workload's generator with fewer nonzeros")
     p.add_argument("--mttkrp-only", action="store_true",
@@ -375,6 +376,37 @@ def run_ours(args, rank, world, local):
                 "kernel": "alto MTTKRP (all modes, incl. output zeroing)",
                 "bytes_per_launch": {str(n): int(per_mode_bytes[n]) for n in range(N)}}
 
+    # CP-ALS seconds per iteration with BF16 factor storage against the plain
+    # FP32 form, on one created tensor (the same iterations, creation excluded)
+    precision = None
+    if fdtype == "f32" and not args.no_bf16:
+        at = AltoTensor(dims, idx_d, vals_d, allocator=alloc, variants=variants, nparts=int(args.nparts))
+        res = {}
+        for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+            U = [u.to(dt) for u in U0_d]
+            W = [torch.empty_like(u) for u in U]
+            for w, u in zip(W, U):
+                w.copy_(u)
+            at.cpals(W, 2, lam=lam)  # warm-up
+            reps, tot, fl = 3, 0.0, None
+            for _ in range(reps):
+                for w, u in zip(W, U):
+                    w.copy_(u)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, fl = at.cpals(W, iters, lam=lam)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            res[name] = (tot / reps / 1e3 / iters, fl[-1] if fl else None)
+            del U, W
+        at.close()
+        precision = {"f32_s_per_iter": res["f32"][0], "bf16_s_per_iter": res["bf16"][0],
+                     "bf16_speedup": res["f32"][0] / res["bf16"][0],
+                     "fit_f32": res["f32"][1], "fit_bf16": res["bf16"][1],
+                     "note": "CP-ALS only (MTTKRP sweeps + updates), one created tensor, 3 timed runs"}
+
     # end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -430,6 +462,7 @@ def run_ours(args, rank, world, local):
                    "calls": [int(c) for c in prof_calls]},
         "create_ms": create_ms,
         "cpals_s_per_iter": cpals_ms / 1e3 / iters,
+        "cpals_precision": precision,
         "fit_last": fits[-1] if fits else None,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -469,6 +469,173 @@ __global__ void __launch_bounds__(kT) normalize_gram_rows_kernel(
   }
 }
 
+// R <= 32 (one column per lane): the same two passes with the rows a warp
+// works on staged in shared memory, so that each lane reads four (FP32) or
+// two (FP64) of a row's values with one broadcast 16-byte load instead of one
+// shuffle per value.  Capped at 64 registers (4 blocks per SM); the Gram pass
+// uses this form for R <= 16 only (at R = 32 its registers spill).
+template <typename C>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+  __device__ static float at(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+  __device__ static double at(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+};
+
+// A = Mt V^{-1} with the column statistics (R in {8, 16, 32}).
+template <typename C, int R>
+__global__ void __launch_bounds__(kT, 4) solve_rows_bcast_kernel(const C* __restrict__ Mt, int64_t I,
+                                                              const C* __restrict__ vinv, C* __restrict__ A,
+                                                              double* __restrict__ colstat, int use_max) {
+  using L = RowLanes<R>;
+  using V = Vec16<C>;
+  static_assert(L::CPL == 1, "one column per lane");
+  constexpr int NB = L::NB;
+  constexpr int ROWS = NB * L::RPW;  // rows a warp stages per iteration
+  __shared__ __align__(16) C sM[kT / 32][ROWS * R];
+  __shared__ double red[kT / 32][R];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / L::W, j = lane % L::W;
+  C v[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = vinv[k * R + j];
+  C stat = C(0);
+  C* my = sM[warp];
+  const int64_t wid = static_cast<int64_t>(blockIdx.x) * (kT / 32) + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kT / 32);
+  for (int64_t r0 = wid * ROWS; r0 < I; r0 += nw * ROWS) {
+    const int64_t e0 = r0 * R;
+    const int64_t e1 = (I < r0 + ROWS ? I : r0 + ROWS) * R;
+#pragma unroll
+    for (int e = lane; e < ROWS * R; e += 32) my[e] = e0 + e < e1 ? Mt[e0 + e] : C(0);
+    __syncwarp();
+    C acc[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[b] = C(0);
+#pragma unroll
+    for (int k = 0; k < R; k += V::N) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const typename V::T x = *reinterpret_cast<const typename V::T*>(my + (b * L::RPW + grp) * R + k);
+#pragma unroll
+        for (int i = 0; i < V::N; ++i) acc[b] = fma(V::at(x, i), v[k + i], acc[b]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t row = r0 + b * L::RPW + grp;
+      if (row < I) {
+        A[row * R + j] = acc[b];
+        stat = use_max ? fmax(stat, fabs(acc[b])) : fma(acc[b], acc[b], stat);
+      }
+    }
+  }
+  double st = static_cast<double>(stat);
+  for (int o = L::W; o < 32; o <<= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, st, o);
+    st = use_max ? fmax(st, y) : st + y;
+  }
+  if (grp == 0) red[warp][j] = st;
+  __syncthreads();
+  for (int c = threadIdx.x; c < R; c += kT) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t = use_max ? fmax(t, red[w][c]) : t + red[w][c];
+    if (use_max)
+      atomic_max_nonneg(colstat + c, t);
+    else
+      atomicAdd(colstat + c, t);
+  }
+}
+
+// U = A / lambda (stored as FT), G += U^T U, optionally the fit's inner
+// product (R in {8, 16, 32}).
+template <typename FT, int R>
+__global__ void __launch_bounds__(kT, 4) normalize_gram_bcast_kernel(
+    const typename CT<FT>::type* __restrict__ A, int64_t I, const double* __restrict__ colstat, int use_max,
+    double* __restrict__ lambda, FT* __restrict__ U, double* __restrict__ G,
+    const typename CT<FT>::type* __restrict__ Mt, double* __restrict__ ip) {
+  using C = typename CT<FT>::type;
+  using L = RowLanes<R>;
+  using V = Vec16<C>;
+  static_assert(L::CPL == 1, "one column per lane");
+  constexpr int NB = L::NB;
+  constexpr int ROWS = NB * L::RPW;
+  __shared__ __align__(16) C sU[kT / 32][ROWS * R];
+  __shared__ C inv[R];
+  __shared__ double lam[R];
+  __shared__ double gred[R * R];
+  __shared__ double ipred[kT / 32];
+  for (int r = threadIdx.x; r < R; r += kT) {
+    const double l = use_max ? fmax(colstat[r], 1.0) : sqrt(colstat[r]);
+    lam[r] = l;
+    inv[r] = static_cast<C>(1.0 / l);
+    if (blockIdx.x == 0) lambda[r] = l;
+  }
+  for (int e = threadIdx.x; e < R * R; e += kT) gred[e] = 0.0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / L::W, j = lane % L::W;
+  const C invj = inv[j];
+  const double lamj = lam[j];
+  C g[R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) g[a] = C(0);
+  double ipd = 0.0;
+  C* my = sU[warp];
+  const int64_t wid = static_cast<int64_t>(blockIdx.x) * (kT / 32) + warp;
+  const int64_t nw = static_cast<int64_t>(gridDim.x) * (kT / 32);
+  for (int64_t r0 = wid * ROWS; r0 < I; r0 += nw * ROWS) {
+    C own[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int64_t row = r0 + b * L::RPW + grp;
+      C u = C(0);
+      if (row < I) {
+        const FT st = static_cast<FT>(A[row * R + j] * invj);
+        U[row * R + j] = st;
+        u = to_ct<FT>(st);
+        if (Mt != nullptr) ipd += static_cast<double>(u * Mt[row * R + j]) * lamj;
+      }
+      own[b] = u;
+      my[(b * L::RPW + grp) * R + j] = u;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < R; a += V::N) {
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const typename V::T x = *reinterpret_cast<const typename V::T*>(my + (b * L::RPW + grp) * R + a);
+#pragma unroll
+        for (int i = 0; i < V::N; ++i) g[a + i] = fma(V::at(x, i), own[b], g[a + i]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    double v = static_cast<double>(g[a]);
+    for (int o = L::W; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (grp == 0) atomicAdd(&gred[a * R + j], v);
+  }
+  for (int o = 16; o > 0; o >>= 1) ipd += __shfl_xor_sync(0xffffffffu, ipd, o);
+  if (lane == 0) ipred[warp] = ipd;
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * R; e += kT) atomicAdd(G + e, gred[e]);
+  if (Mt != nullptr && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += ipred[w];
+    atomicAdd(ip, t);
+  }
+}
+
 // fit = 1 - sqrt(max(0, ||X||^2 + lambda^T (Hadamard G) lambda - 2 ip)) / ||X||
 __global__ void __launch_bounds__(kT) fit_kernel(const double* __restrict__ G, int N, int R,
                                                  const double* __restrict__ lambda, double normX2,
@@ -558,9 +725,9 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
         C* at = static_cast<C*>(w.atmp);
         const unsigned gr = rows_grid(In, 32 * 8, 8);
         switch (R) {
-          case 8: solve_rows_kernel<C, 8><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
-          case 16: solve_rows_kernel<C, 16><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
-          case 32: solve_rows_kernel<C, 32><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 8: solve_rows_bcast_kernel<C, 8><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 16: solve_rows_bcast_kernel<C, 16><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
+          case 32: solve_rows_bcast_kernel<C, 32><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
           case 64: solve_rows_kernel<C, 64><<<gr, kT, 0, s>>>(mt, In, vinv, at, w.colstat, use_max); break;
           default:
             solve_kernel<C><<<rows_grid(In, kT / R, 8), kT, 0, s>>>(mt, In, R, vinv, at, w.colstat, use_max);
@@ -578,8 +745,9 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
         const C* mt = last ? static_cast<const C*>(w.mt) : nullptr;
         const unsigned gr = rows_grid(In, 32 * 8, 8);
         switch (R) {
-          case 8: normalize_gram_rows_kernel<FT, 8><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
-          case 16: normalize_gram_rows_kernel<FT, 16><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          case 8: normalize_gram_bcast_kernel<FT, 8><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          case 16: normalize_gram_bcast_kernel<FT, 16><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
+          // R = 32: the Gram registers leave no room for the staged rows; the shuffle form stays
           case 32: normalize_gram_rows_kernel<FT, 32><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
           case 64: normalize_gram_rows_kernel<FT, 64><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
           default:
