@@ -150,9 +150,15 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=5)
+        return self.parse(self.lines)
+
+    @staticmethod
+    def parse(lines):
+        """Median SM clock, maximum clock and the throttle reasons seen in
+        nvidia-smi CSV lines (the FIELDS order, no header, no units)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
