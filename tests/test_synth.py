@@ -58,3 +58,29 @@ def test_factors_dtype_and_shape():
     f = synth.factors(cfg)
     assert [x.shape for x in f] == [(64, 16), (128, 16), (256, 16)]
     assert all(x.dtype == np.float64 for x in f)
+
+
+def test_torch_generator_draws_distinct_in_range_coordinates():
+    """The device-side generator (run here on the CPU): exact nnz, indices
+    inside their modes, no duplicate coordinate, values in [0, 1), factors
+    of the configured shape; Zipf modes skewed toward few rows."""
+    import numpy as np
+    import torch
+    for seed in (0, 1, 2, 5, 9):
+        cfg = dict(synth.batch_config(seed))
+        cfg["nnz"] = min(cfg["nnz"], 50_000)
+        dims, idx, vals = synth.tensor_torch(cfg, "cpu")
+        M = cfg["nnz"]
+        assert len(vals) == M and all(len(a) == M for a in idx)
+        coords = np.stack([a.numpy().astype(np.int64) for a in idx], 1)
+        assert (coords >= 0).all() and (coords < np.array(dims)).all()
+        assert len(np.unique(coords, axis=0)) == M
+        assert float(vals.min()) >= 0.0 and float(vals.max()) < 1.0
+        U = synth.factors_torch(cfg, "cpu", torch.bfloat16)
+        assert [tuple(u.shape) for u in U] == [(d, cfg["rank"]) for d in dims]
+        assert all(u.dtype == torch.bfloat16 for u in U)
+        if cfg["laws"][0] not in ("uniform", "clustered"):
+            n = int(np.argmax(dims))
+            counts = np.bincount(coords[:, n], minlength=dims[n])
+            top = np.sort(counts)[::-1][: max(1, dims[n] // 100)].sum()
+            assert top > 0.05 * M     # the top 1% of rows hold a visible share
