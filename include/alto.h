@@ -318,10 +318,9 @@ alto_status alto_launch_count(uint64_t *count);
  * alto_linearize_noalloc -- the linearization and ordering stages of
  * alto_create (bit-level encode, stable sort) written into caller buffers,
  * without allocating any device memory.  The paper has no counterpart: this
- * entry point exists for callers that cannot call cudaMalloc, such as code
- * that runs while a stream is being captured into a CUDA graph, services that
- * reserve all device memory for their own pool, and embedders whose device
- * allocator belongs to another runtime.
+ * entry point exists for callers that cannot call cudaMalloc, such as
+ * services that reserve all device memory for their own pool up front and
+ * embedders whose device allocator belongs to another runtime.
  *
  *   idx   : host array of N DEVICE pointers to nnz indices (idx_bytes 4 or 8).
  *   keys  : device, nnz x key_words uint64 (key_words from
@@ -330,11 +329,13 @@ alto_status alto_launch_count(uint64_t *count);
  * The sort's scratch lives in one fixed device array of about 5.3 MB that
  * every GPU which loads libalto holds until the process exits; nnz above
  * ALTO_NOALLOC_MAX_NNZ is rejected with ALTO_EINVAL.  The first call on each
- * device looks up that array's device address, so make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
- * streams, other host threads on the same device) race and must be
- * serialised by the caller.  Synchronises `stream` at its end; returns
- * ALTO_ERANGE when an index is out of range.
+ * device looks up that array's device address and keeps it for the life of
+ * the process (do not call it again after resetting the device).  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads on the same device) race and must be serialised by the caller.
+ * The call reads its status word back and synchronises `stream` at its end,
+ * so it cannot run while the stream is being captured into a CUDA graph;
+ * returns ALTO_ERANGE when an index is out of range.
  */
 #define ALTO_NOALLOC_MAX_NNZ 262144
 alto_status alto_linearize_noalloc(int nmodes, const uint64_t *dims,

@@ -18,7 +18,9 @@ What each function follows in the paper:
 * ``flags`` -- Sec. 3.3 last paragraph: internal element = its row along the
   mode is touched by exactly one segment.
 * ``mttkrp`` -- Sec. 2.2 definition, Alg. 1 in COO form: direct FP64
-  summation in input order.
+  summation in input order.  ``mttkrp_threads`` splits the same sums over
+  host threads by output row (bit-identical; used to time the oracle on
+  all host cores).
 * ``cpals`` -- Sec. 2.2 CPD-ALS; the paper defers its conventions to
   SPLATT / Tensor Toolbox, so this is the Kolda-Bader CP-ALS: per mode,
   MTTKRP, Hadamard product of the other Gram matrices, Cholesky solve,
@@ -58,9 +60,10 @@ def _load():
         lib.orc_intervals.argtypes = [i32, i64, P, i64, P, P]
         lib.orc_flags.argtypes = [i32, ctypes.c_uint64, i32, i64, P, i64, P, P]
         lib.orc_mttkrp.argtypes = [i32, P, i64, P, i32, P, P, i32, i32, P, P]
+        lib.orc_mttkrp_threads.argtypes = [i32, P, i64, P, i32, P, P, i32, i32, P, i32]
         for f in (lib.orc_bit_map, lib.orc_encode, lib.orc_decode,
                   lib.orc_sort_perm, lib.orc_partition, lib.orc_intervals,
-                  lib.orc_flags, lib.orc_mttkrp):
+                  lib.orc_flags, lib.orc_mttkrp, lib.orc_mttkrp_threads):
             f.restype = i32
         _lib = lib
     return _lib
@@ -214,6 +217,25 @@ def mttkrp(dims, idx, vals, factors, mode, rows=None):
     lib.orc_mttkrp(N, _ptr(d), M, ptrs, width, _ptr(v), fptrs, R, mode,
                    _ptr(mask) if mask is not None else None, _ptr(out))
     return out
+
+
+def mttkrp_threads(dims, idx, vals, factors, mode, threads):
+    """``mttkrp`` on ``threads`` host threads (each owns the output rows
+    i_n mod T and sums their nonzeros in input order, so the result is
+    bit-identical to ``mttkrp``).  Returns (out, threads used)."""
+    lib = _load()
+    d = _dims(dims)
+    N = len(d)
+    arrs, ptrs, width = _idx_arrays(idx)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    fs = [None if (m == mode or factors[m] is None) else np.ascontiguousarray(factors[m], dtype=np.float64)
+          for m in range(N)]
+    R = next(f.shape[1] for f in fs if f is not None)
+    fptrs = (ctypes.c_void_p * N)(*[(f.ctypes.data if f is not None else 0) for f in fs])
+    out = np.zeros((int(d[mode]), R), dtype=np.float64)
+    used = lib.orc_mttkrp_threads(N, _ptr(d), v.shape[0], ptrs, width, _ptr(v), fptrs, R, mode, _ptr(out),
+                                  int(threads))
+    return out, used
 
 
 def reuse(dims, M):

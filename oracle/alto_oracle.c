@@ -25,6 +25,12 @@
  *                    one segment).
  *   orc_mttkrp       Sec. 2.2 definition / Alg. 1 in COO form: direct
  *                    summation out[i_n][r] += v * prod_{m!=n} U_m[i_m][r].
+ *   orc_mttkrp_threads  the same sums on several host threads: thread t
+ *                    owns the output rows i_n with i_n mod T == t and adds
+ *                    their nonzeros in input order, so every output row is
+ *                    the same sequence of FP64 additions as in orc_mttkrp
+ *                    (bit-identical results); only used to time the oracle
+ *                    on all host cores.
  *
  * Keys are always held as two 64-bit words per nonzero (lo, hi), whatever
  * the word width the product path picks.
@@ -32,6 +38,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXN 16
 #define ORC_MAXB 128
@@ -307,4 +316,50 @@ int orc_mttkrp(int N, const uint64_t *dims, int64_t M, const void *const *idx,
         }
     }
     return 0;
+}
+
+/*
+ * orc_mttkrp on `threads` host threads (OpenMP): every thread reads all
+ * nonzeros and accumulates those whose output row it owns (i_n mod T), in
+ * input order.  Each output element receives the same additions in the same
+ * order as in orc_mttkrp.  Returns the number of threads used.
+ */
+int orc_mttkrp_threads(int N, const uint64_t *dims, int64_t M, const void *const *idx,
+                       int idx_bytes, const double *vals, const double *const *factors,
+                       int R, int n, double *out, int threads)
+{
+    int used = 1;
+    if (threads < 1)
+        threads = 1;
+    memset(out, 0, sizeof(double) * (size_t)dims[n] * (size_t)R);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(threads)
+    {
+        const uint64_t T = (uint64_t)omp_get_num_threads();
+        const uint64_t me = (uint64_t)omp_get_thread_num();
+        int64_t x;
+        int m, r;
+        uint64_t i[ORC_MAXN];
+#pragma omp single
+        used = (int)T;
+        for (x = 0; x < M; x++) {
+            const uint64_t row = read_index(idx[n], idx_bytes, x);
+            if (row % T != me)
+                continue;
+            for (m = 0; m < N; m++)
+                i[m] = read_index(idx[m], idx_bytes, x);
+            for (r = 0; r < R; r++) {
+                double t = vals[x];
+                for (m = 0; m < N; m++)
+                    if (m != n)
+                        t *= factors[m][i[m] * (uint64_t)R + r];
+                out[row * (uint64_t)R + r] += t;
+            }
+        }
+    }
+#else
+    (void)threads;
+    orc_mttkrp(N, dims, M, idx, idx_bytes, vals, factors, R, n, NULL, out);
+#endif
+    return used;
 }

@@ -22,7 +22,7 @@ def build(force=False):
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, SRC]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, SRC]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -34,6 +34,14 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
 
 namespace {
 
+// the input factors of a mode-`mode` MTTKRP in kernel slot order
+std::vector<const void*> factors_in_slot_order(const alto_tensor_s* t, int mode, const void* const* f) {
+  std::vector<const void*> r;
+  for (int m = 0; m < t->lay.N; ++m)
+    if (m != mode) r.push_back(f[m]);
+  return r;
+}
+
 constexpr int kBatchHotReplicas = 8;
 constexpr int kBatchHotCap = 256;
 constexpr size_t kBatchBranches = 16;  // parallel branches of the graph
@@ -87,7 +95,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
   cudaError_t e = cudaSuccess;
 
   // item descriptions, grouped by kernel shape
-  using Key = std::tuple<int, int, int, int>;  // N, KW, R, variant
+  using Key = std::tuple<int, int, int, int, int>;  // N, KW, R, variant, fused body
   struct Zero {
     void* p;
     size_t bytes;
@@ -117,7 +125,10 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
       single.push_back(i);
       continue;
     }
-    const Key key{t->lay.N, t->lay.KW, R, v};
+    const int fused = (v == ALTO_VAR_ATOMIC || v == ALTO_VAR_WARPAGG) &&
+                      fused_ok(t->lay.N, R, fsz, factors_in_slot_order(t, mode, factors[i]).data(), outs[i], osz,
+                               t->lay.dims[mode]);
+    const Key key{t->lay.N, t->lay.KW, R, v, fused};
     HostGroup& hg = groups[key];
     hg.zeros.push_back(z);
     hg.cost += static_cast<double>(t->M) * (8.0 * t->lay.KW + 4.0 + (t->lay.N - 1) * R * fsz) +
@@ -236,6 +247,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     bl.sms = sms;
     bl.smem_dyn = g.host->smem;
     bl.units = g.units;
+    bl.fused = std::get<4>(g.key) != 0;
     e = mttkrp_batch_dispatch(bl, fdtype, bs);
   }
   for (size_t k = 0; e == cudaSuccess && k < single.size(); ++k) {

@@ -131,6 +131,11 @@ void dev_free(alto_tensor_s* t, void* p);
 alto_status fail(alto_status code, const char* fmt, ...);
 
 // sort.cu
+// Key bits per radix-sort pass, and the passes radix_sort_pairs makes over
+// nbits key bits (at least one, so that the position array is always written;
+// the result lands in the first buffer pair after an even number of passes).
+constexpr int kSortDigitBits = 8;
+constexpr int sort_passes_for(int nbits) { return nbits > 0 ? (nbits + kSortDigitBits - 1) / kSortDigitBits : 1; }
 // 32-bit words of sort scratch (tile counts, offsets, scan partials) for M keys
 constexpr int64_t sort_scratch_words_for(int64_t M) {
   return 2 * (((M + 4095) / 4096) * 256) + ((((M + 4095) / 4096) * 256 + 8191) / 8192) + 64;

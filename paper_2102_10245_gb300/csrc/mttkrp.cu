@@ -134,6 +134,9 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
   if (v == ALTO_VAR_TEMP) return launch_temp_variant(t, l, fdtype, osz, s);
   if (!mttkrp_specialised(N, R)) v = ALTO_VAR_ATOMIC;  // the generic kernel
   l.variant = v;
+  const size_t fsz = fdtype == ALTO_F64 ? 8 : (fdtype == ALTO_F32 ? 4 : 2);
+  l.fused = (v == ALTO_VAR_ATOMIC || v == ALTO_VAR_WARPAGG) && mttkrp_specialised(N, R) &&
+            fused_ok(N, R, fsz, l.args.f, out, osz, lay.dims[mode]);
   int H = 0;
   if (v == ALTO_VAR_WARPAGG && lay.dims[mode] <= (1ull << 31) && mttkrp_specialised(N, R)) {
     H = t->hot_n[mode];

@@ -672,19 +672,37 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
   }
 }
 
+}  // namespace alto
+
+#include "mttkrp_fused.cuh"
+
+namespace alto {
+
 // One MTTKRP: persistent blocks stride over the units.
-template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads, 4) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
+// FUSED selects the fused body (ATOMIC / WARPAGG only), which holds more
+// gathers in flight and therefore runs fewer, larger-register blocks per SM.
+#ifndef ALTO_FUSED_BLOCKS
+#define ALTO_FUSED_BLOCKS 2
+#endif
+constexpr int kFusedBlocks = ALTO_FUSED_BLOCKS;
+
+template <int N, int KW, int R, typename FT, int POL, bool FUSED = false>
+__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
   __shared__ uint32_t s_lorows[2];
   extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ uint4 s_stage2[FUSED ? 2 : 1][kWarps][32][Stage<N, VT>::W4];
   BlockState<AT> st{0, nullptr, nullptr, nullptr};
   if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(a, dyn, blockIdx.x % kHotReplicas);
   const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x)
-    process_unit<N, KW, R, FT, POL>(a, u, st, s_stage, s_lorows, dyn);
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    if constexpr (FUSED && (POL == kAtomic || POL == kWarpAgg))
+      process_unit_fused<N, KW, R, FT, POL>(a, u, st, s_stage2);
+    else
+      process_unit<N, KW, R, FT, POL>(a, u, st, s_stage, s_lorows, dyn);
+  }
 }
 
 // Many MTTKRPs of one kernel shape in one persistent launch (the batched
@@ -699,13 +717,14 @@ struct BatchArgs {
   int hot_replicas;            // copies of each item's hot rows
 };
 
-template <int N, int KW, int R, typename FT, int POL>
-__global__ void __launch_bounds__(kThreads, 4) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
+template <int N, int KW, int R, typename FT, int POL, bool FUSED = false>
+__global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   __shared__ uint4 s_stage[kWarps][32][Stage<N, VT>::W4];
   __shared__ uint32_t s_lorows[2];
   __shared__ __align__(16) MttkrpArgs s_args;
+  __shared__ uint4 s_stage2[FUSED ? 2 : 1][kWarps][32][Stage<N, VT>::W4];
   extern __shared__ __align__(16) unsigned char dyn[];
   const int64_t total = b.unit_prefix[b.nitems];
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
@@ -732,7 +751,10 @@ __global__ void __launch_bounds__(kThreads, 4) mttkrp_batch_kernel(const __grid_
       __syncthreads();
       if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(s_args, dyn, blockIdx.x % b.hot_replicas);
     }
-    process_unit<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage, s_lorows, dyn);
+    if constexpr (FUSED && (POL == kAtomic || POL == kWarpAgg))
+      process_unit_fused<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage2);
+    else
+      process_unit<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage, s_lorows, dyn);
   }
 }
 
@@ -831,6 +853,7 @@ struct MttkrpLaunch {
   int variant;   // ATOMIC / WARPAGG / SMEM / TEMP (the generic kernel ignores it)
   int sms;       // SM count of the device
   size_t smem_dyn;
+  bool fused;    // ATOMIC / WARPAGG through the fused body
 };
 
 cudaError_t mttkrp_dispatch_f32_k1(const MttkrpLaunch& l, cudaStream_t s);
@@ -850,6 +873,7 @@ struct BatchLaunch {
   int sms;
   size_t smem_dyn;
   int64_t units;  // thread-block units of all items
+  bool fused;     // ATOMIC / WARPAGG through the fused body
 };
 
 cudaError_t mttkrp_batch_dispatch_f32_k1(const BatchLaunch& l, cudaStream_t s);
@@ -896,8 +920,12 @@ cudaError_t mttkrp_batch_dispatch_typed(const BatchLaunch& l, cudaStream_t s) {
   do {                                                                                           \
     switch (l.variant) {                                                                         \
       case kSmem: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kSmem>, l, s);          \
-      case kAtomic: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic>, l, s);      \
-      default: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg>, l, s);          \
+      case kAtomic:                                                                              \
+        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic, true>, l, s); \
+        return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic>, l, s);                  \
+      default:                                                                                   \
+        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg, true>, l, s); \
+        return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg>, l, s);                 \
     }                                                                                            \
   } while (0)
 #define ALTO_BLAUNCH_R(NN)              \
@@ -961,8 +989,12 @@ cudaError_t mttkrp_dispatch_typed(const MttkrpLaunch& l, cudaStream_t s) {
     switch (l.variant) {                                                                                 \
       case kSmem: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kSmem>, l, l.smem_dyn, units, s); \
       case kTemp: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kTemp>, l, 0, units, s);        \
-      case kWarpAgg: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg>, l, l.smem_dyn, units, s); \
-      default: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic>, l, 0, units, s);         \
+      case kWarpAgg:                                                                                     \
+        if (l.fused) return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg, true>, l, l.smem_dyn, units, s); \
+        return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg>, l, l.smem_dyn, units, s);    \
+      default:                                                                                           \
+        if (l.fused) return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic, true>, l, 0, units, s); \
+        return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic>, l, 0, units, s);              \
     }                                                                                                    \
   } while (0)
 #define ALTO_LAUNCH_R(NN)              \

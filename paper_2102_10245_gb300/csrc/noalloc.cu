@@ -2,13 +2,15 @@
 // buffers, with every scratch buffer in one fixed, file-scope device array,
 // so the call never allocates device memory.
 //
-// Some callers cannot allocate: code that runs while a stream is being
-// captured into a CUDA graph (cudaMalloc is not allowed there), services that
-// pre-reserve all device memory for their own pool, and embedders whose
-// allocator is owned by another runtime.  They still pass their own inputs and
-// outputs; this entry point supplies the sort's scratch itself.
+// Some callers cannot allocate: services that reserve all device memory for
+// their own pool up front, and embedders whose device allocator belongs to
+// another runtime (a cudaMalloc behind its back would break its accounting).
+// They still pass their own inputs and outputs; this entry point supplies the
+// sort's scratch itself.  The call reads its status word back and
+// synchronises the stream, so it cannot be recorded into a CUDA graph.
 //
-// The array is kNoAllocBytes of device memory that every GPU which loads
+// The array is kScratchWords 8-byte words (about 5.3 MB) of device memory
+// that every GPU which loads
 // libalto keeps until the process exits.  All calls share it: two calls whose
 // work overlaps on the GPU (different streams, or different host threads on
 // one device) race on it and must be serialised by the caller.
@@ -37,7 +39,9 @@ void* g_scratch_addr[64] = {};
 
 // Device address of the scratch array for the current device.  The array's
 // name in host code only stands in for the symbol; the address the kernels
-// need is looked up once per device.
+// need is looked up once per device (the first call on that device) and kept
+// for the life of the process, so a caller that resets the device
+// (cudaDeviceReset) must not call this entry point afterwards.
 alto_status scratch_for_current_device(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -89,7 +93,7 @@ extern "C" alto_status alto_linearize_noalloc(int nmodes, const uint64_t* dims, 
 
   // The sort ping-pongs between two buffers; start in the scratch one when the
   // pass count is odd so that the result lands in the caller's buffers.
-  const int passes = lay.B > 0 ? (lay.B + 7) / 8 : 1;
+  const int passes = sort_passes_for(lay.B);
   uint64_t* k0 = (passes & 1) ? key_alt : keys;
   uint64_t* k1 = (passes & 1) ? keys : key_alt;
   uint32_t* p0 = (passes & 1) ? perm_alt : perm;

@@ -21,7 +21,7 @@ namespace alto {
 
 namespace {
 
-constexpr int kDigitBits = 8;
+constexpr int kDigitBits = kSortDigitBits;
 constexpr int kRadix = 1 << kDigitBits;
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -282,10 +282,9 @@ cudaError_t radix_sort_pairs(uint64_t** keys, uint64_t** keys_alt, uint32_t** pe
   uint32_t* counts = scratch;
   uint32_t* offsets = scratch + ncount;
   uint32_t* part = scratch + 2 * ncount;
-  const int passes = (nbits + kDigitBits - 1) / kDigitBits;
+  const int passes = sort_passes_for(nbits);
   bool iota = true;
-  for (int p = 0; p < passes || iota; ++p) {
-    // at least one pass, so that the position array is always written
+  for (int p = 0; p < passes; ++p) {
     const int shift = p * kDigitBits;
     if (KW == 1) {
       tile_histogram<1><<<static_cast<unsigned>(ntiles), kSortThreads, 0, s>>>(*keys, M, shift, ntiles,

@@ -457,3 +457,18 @@ def test_cpals_fit_matches_explicit_residual_and_is_monotone():
     explicit = 1 - np.linalg.norm(X - model) / np.linalg.norm(X)
     assert abs(fits[-1] - explicit) < 1e-9
     assert all(b >= a - 1e-9 for a, b in zip(fits, fits[1:]))
+
+
+def test_threaded_mttkrp_is_bit_identical():
+    """The host-thread MTTKRP used for the multi-core CPU baseline performs the
+    same additions per output element in the same order as the serial oracle."""
+    import synth
+    cfg = synth.scaled("zipf3d-4Mx4Mx30k", nnz=50_000)
+    dims, idx, vals = synth.tensor(cfg)
+    rng = np.random.default_rng(5)
+    U = [rng.standard_normal((d, 8)) for d in dims]
+    for n in range(3):
+        a = oracle.mttkrp(dims, idx, vals, U, n)
+        b, used = oracle.mttkrp_threads(dims, idx, vals, U, n, 4)
+        assert used >= 1
+        assert np.array_equal(a, b)
