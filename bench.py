@@ -37,7 +37,10 @@ import synth  # noqa: E402
 METRIC = "all-mode MTTKRP Gnnz/s + % HBM roofline; CP-ALS s/iter vs plain FP32"
 DEFAULT_CONFIG = "zipf3d-4Mx4Mx30k"
 FALLBACK_HBM_GBS = 6800.0
-CPU_SAMPLE_NNZ = 20_000_000      # oracle CPU-baseline sample (about 15-20 s)
+CPU_SAMPLE_NNZ = 40_000_000      # oracle CPU-baseline sample, all host threads
+CPU_SAMPLE_NNZ_1T = 10_000_000   # the same, one thread (about 8-10 s)
+GEN_SAMPLE_NNZ = 10_000_000      # oracle generation sample (encode + sort)
+RANKSPEC_NNZ = 20_000_000        # rank-specialisation comparison tensor
 REF_STEP_NNZ = 4_000_000         # reference-arm step sample
 
 
@@ -54,6 +57,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true", help="skip the BF16-factor CP-ALS comparison")
+    p.add_argument("--no-rankspec", action="store_true", help="skip the rank-specialisation comparison")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched + learned sub-measurement")
+    p.add_argument("--sub-batch-items", type=int, default=64,
+                   help="held-out batched tensors in the default line's batched sub-measurement")
     p.add_argument("--nnz", type=int, default=0,
                    help="profiling only: the workload's generator with fewer nonzeros")
     p.add_argument("--mttkrp-only", action="store_true",
@@ -189,15 +196,10 @@ def measured_peak():
 
 
 def kernel_source_hash():
-    """Hash of the MTTKRP kernel sources (a recorded ncu traffic figure is
-    only reported while it matches)."""
-    import glob
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2102_10245_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "mttkrp*")) + [os.path.join(csrc, "common.cuh")])
-    for f in files:
-        h.update(open(f, "rb").read())
-    return h.hexdigest()[:16]
+    """Hash of the MTTKRP kernel sources (a recorded ncu traffic figure or
+    timing set is only used while it matches)."""
+    import paper_2102_10245_gb300.build as lb
+    return lb.kernel_source_hash()
 
 
 def recorded_traffic(config, fdtype, calls):
@@ -240,6 +242,54 @@ def oracle_sweep_time(dims, idx, vals, U64, nnz_sample):
     for n in range(len(dims)):
         oracle.mttkrp(dims, sidx, sv, U64, n)
     return time.perf_counter() - t0
+
+
+def oracle_sweep_time_threads(dims, idx, vals, U64, nnz_sample, threads):
+    """The oracle's all-mode MTTKRP on `threads` host threads (each owns the
+    output rows i_n mod T; bit-identical to the single-thread sums).
+    Returns (seconds, threads used)."""
+    import oracle
+    sidx = [a[:nnz_sample] for a in idx]
+    sv = np.asarray(vals[:nnz_sample], dtype=np.float64)
+    used = 1
+    t0 = time.perf_counter()
+    for n in range(len(dims)):
+        _, used = oracle.mttkrp_threads(dims, sidx, sv, U64, n, threads)
+    return time.perf_counter() - t0, used
+
+
+def oracle_generation_time(dims, idx, nnz_sample):
+    """The oracle's linearization and ordering (bit-loop encode, stable sort
+    by key with an index tie-break) on one host thread; seconds."""
+    import oracle
+    sidx = [a[:nnz_sample] for a in idx]
+    t0 = time.perf_counter()
+    keys = oracle.encode(dims, sidx)
+    oracle.sort_perm(keys)
+    return time.perf_counter() - t0
+
+
+def host_cpu():
+    """Host CPU model and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
 
 
 def run_reference(args, rank, world):
@@ -287,13 +337,26 @@ def run_ours(args, rank, world, local):
 
     # CPU baseline first (rank 0, single GPU only), before any GPU work
     cpu = None
+    gen_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S = min(CPU_SAMPLE_NNZ, M)
         U64 = [u.astype(np.float64) for u in U0]
-        t = oracle_sweep_time(dims, idx, vals, U64, S)
-        cpu = {"value": N * S / t / 1e9, "unit": "Gnnz/s", "cores": 1, "kind": "oracle",
-               "sample": "all-mode FP64 COO MTTKRP (the oracle) over the first %d of %d nonzeros, "
-                         "single thread, %.1f s" % (S, M, t)}
+        hc = host_cpu()
+        nth = max(1, int(hc["nproc"] or 1))
+        tm, used = oracle_sweep_time_threads(dims, idx, vals, U64, S, nth)
+        t1 = oracle_sweep_time(dims, idx, vals, U64, min(S, CPU_SAMPLE_NNZ_1T))
+        S1 = min(S, CPU_SAMPLE_NNZ_1T)
+        cpu = {"value": N * S / tm / 1e9, "unit": "Gnnz/s", "cores": used, "kind": "oracle",
+               "cpu": hc["model"], "nproc": hc["nproc"],
+               "sample": "all-mode FP64 COO MTTKRP (the oracle) over the first %d of %d nonzeros on %d host "
+                         "threads (output rows split by thread, bit-identical sums), %.1f s" % (S, M, used, tm),
+               "single_thread": {"value": N * S1 / t1 / 1e9, "unit": "Gnnz/s", "cores": 1,
+                                 "sample": "the same on one thread over the first %d nonzeros, %.1f s" % (S1, t1)}}
+        SG = min(GEN_SAMPLE_NNZ, M)
+        tg = oracle_generation_time(dims, idx, SG)
+        gen_oracle = {"gnnz_s": SG / tg / 1e9, "cores": 1, "seconds": tg,
+                      "sample": "oracle encode (bit loops) + stable sort (qsort, index tie-break) of the first "
+                                "%d nonzeros, one thread" % SG}
         del U64
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -382,18 +445,24 @@ def run_ours(args, rank, world, local):
                 "kernel": "alto MTTKRP (all modes, incl. output zeroing)",
                 "bytes_per_launch": {str(n): int(per_mode_bytes[n]) for n in range(N)}}
 
-    # CP-ALS seconds per iteration with BF16 factor storage against the plain
-    # FP32 form, on one created tensor (the same iterations, creation excluded)
+    # CP-ALS seconds per iteration and MTTKRP sweep time with BF16 factor
+    # storage, and with BF16 values plus BF16 factors, against the plain FP32
+    # form (the same iterations, creation excluded)
     precision = None
     if fdtype == "f32" and not args.no_bf16:
-        at = AltoTensor(dims, idx_d, vals_d, allocator=alloc, variants=variants, nparts=int(args.nparts))
+        at32 = AltoTensor(dims, idx_d, vals_d, allocator=alloc, variants=variants, nparts=int(args.nparts))
+        at16 = AltoTensor(dims, idx_d, vals_d.to(torch.bfloat16), allocator=alloc, variants=variants,
+                          nparts=int(args.nparts))
         res = {}
-        for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        for name, at_, dt in (("f32", at32, torch.float32), ("bf16", at32, torch.bfloat16),
+                              ("bf16_values", at16, torch.bfloat16)):
             U = [u.to(dt) for u in U0_d]
             W = [torch.empty_like(u) for u in U]
             for w, u in zip(W, U):
                 w.copy_(u)
-            at.cpals(W, 2, lam=lam)  # warm-up
+            at_.cpals(W, 2, lam=lam)  # warm-up
+            at_.profile(True)
+            at_.profile_read()
             reps, tot, fl = 3, 0.0, None
             for _ in range(reps):
                 for w, u in zip(W, U):
@@ -401,17 +470,54 @@ def run_ours(args, rank, world, local):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                _, fl = at.cpals(W, iters, lam=lam)
+                _, fl = at_.cpals(W, iters, lam=lam)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 tot += e0.elapsed_time(e1)
-            res[name] = (tot / reps / 1e3 / iters, fl[-1] if fl else None)
+            pms, pcalls = at_.profile_read()
+            at_.profile(False)
+            res[name] = (tot / reps / 1e3 / iters, fl[-1] if fl else None,
+                         float(pms.sum()) / max(1, int(pcalls.min())))
             del U, W
-        at.close()
+        at32.close()
+        at16.close()
         precision = {"f32_s_per_iter": res["f32"][0], "bf16_s_per_iter": res["bf16"][0],
+                     "bf16_values_s_per_iter": res["bf16_values"][0],
                      "bf16_speedup": res["f32"][0] / res["bf16"][0],
-                     "fit_f32": res["f32"][1], "fit_bf16": res["bf16"][1],
-                     "note": "CP-ALS only (MTTKRP sweeps + updates), one created tensor, 3 timed runs"}
+                     "bf16_values_speedup": res["f32"][0] / res["bf16_values"][0],
+                     "mttkrp_sweep_ms": {k: v[2] for k, v in res.items()},
+                     "fit_f32": res["f32"][1], "fit_bf16": res["bf16"][1], "fit_bf16_values": res["bf16_values"][1],
+                     "note": "CP-ALS only (MTTKRP sweeps + updates), one created tensor per value dtype, 3 timed "
+                             "runs; bf16 = BF16 factor storage, bf16_values = BF16 values and BF16 factors, FP32 "
+                             "accumulation throughout"}
+
+    # rank specialisation (Sec. 4.5): the rank- and order-specialised fused
+    # kernel against the runtime-rank generic kernel, on a smaller tensor
+    # of the same generator, every mode, FP32 factors
+    rankspec = None
+    if not args.no_rankspec:
+        rcfg = synth.scaled(args.config, nnz=min(RANKSPEC_NNZ, M))
+        rdims, ridx, rvals = synth.tensor_torch(rcfg, dev)
+        at = AltoTensor(rdims, ridx, rvals, allocator=alloc)
+        del ridx
+        res = {}
+        for Rr in (8, 16, 32, 64):
+            U = synth.factors_torch(dict(rcfg, rank=Rr), dev, torch.float32)
+            outs = [torch.empty(d, Rr, dtype=torch.float32, device=dev) for d in rdims]
+            t = {}
+            for name, var in (("specialised", 0), ("generic", 5)):
+                for n in range(N):
+                    at.set_variant(n, var)
+                sweep = lambda: [at.mttkrp(n, U, out=outs[n]) for n in range(N)]  # noqa: E731
+                sweep()
+                t[name] = _time_k(sweep, 3, stream)
+            res[str(Rr)] = {"specialised_ms": t["specialised"], "generic_ms": t["generic"],
+                            "ratio": t["generic"] / t["specialised"]}
+            del U, outs
+        at.close()
+        rankspec = {"nnz": int(len(rvals)), "per_rank": res,
+                    "what": "all-mode MTTKRP sweep, FP32 factors: specialised (order and rank fixed at compile "
+                            "time, fused body) vs generic (runtime order and rank, scalar atomics)"}
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -452,6 +558,16 @@ def run_ours(args, rank, world, local):
         e2e = {"value": units / (ms_e2e / 1e3) / 1e9, "unit": "Gnnz/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e, "steps": k2}
 
+    batched = None
+    if not args.no_batched:
+        sub = run_batched(args, rank, world, local, n_items=args.sub_batch_items, steps=3, emit=False)
+        if sub is not None:
+            batched = {k: sub[k] for k in ("value", "unit", "ms_per_step", "config", "plain_fp32",
+                                           "speedup_vs_plain_fp32", "speedup_vs_fp32_batched", "context",
+                                           "predictor", "rel_err_vs_fp64",
+                                           "batch", "roofline")}
+            batched["form"] = "BF16 factors, every (tensor, mode) in one graph, predictor picks"
+
     if rank != 0:
         return
     line = {
@@ -467,8 +583,14 @@ def run_ours(args, rank, world, local):
                    "ms_per_mode": [float(prof_ms[n] / max(1, prof_calls[n])) for n in range(N)],
                    "calls": [int(c) for c in prof_calls]},
         "create_ms": create_ms,
+        "generation": {"gnnz_s": M / (create_ms / 1e3) / 1e9, "ms": create_ms,
+                       "what": "alto_create from HBM-resident COO: encode, radix sort, value permutation, "
+                               "partition and intervals, statistics, flags",
+                       "oracle": gen_oracle},
         "cpals_s_per_iter": cpals_ms / 1e3 / iters,
         "cpals_precision": precision,
+        "rank_specialisation": rankspec,
+        "batched": batched,
         "fit_last": fits[-1] if fits else None,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -495,7 +617,7 @@ def _time_k(fn, k, stream):
     return e0.elapsed_time(e1) / k
 
 
-def run_batched(args, rank, world, local):
+def run_batched(args, rank, world, local, n_items=None, steps=None, emit=True):
     """The batched + learned workload: all-mode MTTKRP of 256 seeded tensors
     of order 3-5 (nnz 10k-5M, lengths 100-10M, uniform / Zipf / clustered,
     R in {8, 16, 32, 64}).  Headline: BF16 factors, every (tensor, mode) in
@@ -509,11 +631,11 @@ def run_batched(args, rank, world, local):
     lb.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    K, W = args.steps, max(args.warmup, 0)
+    K, W = (steps or args.steps), max(args.warmup, 0)
     log = lambda m: print("[batched %.0fs] %s" % (time.time() - t_start, m), file=sys.stderr, flush=True)  # noqa
     t_start = time.time()
 
-    seeds = list(range(BATCH_HELDOUT, BATCH_HELDOUT + args.batch_items))
+    seeds = list(range(BATCH_HELDOUT, BATCH_HELDOUT + (n_items or args.batch_items)))
     cfgs = [synth.batch_config(s) for s in seeds]
     tensors = []
     for cfg in cfgs:
@@ -556,9 +678,18 @@ def run_batched(args, rank, world, local):
     rule = np.array([tune.rule_pick(at, n, U[0].shape[1]) for at, n, U, _ in items])
 
     # the predictor: trained on the GPU by libalto's nn kernels
+    timing_set = None
     if os.path.exists(TIMINGS):
         d = np.load(TIMINGS)
         tr_f, tr_t, src = d["train_features"], d["train_times"], os.path.relpath(TIMINGS, ROOT)
+        stored = str(d["kernel_hash"]) if "kernel_hash" in d.files else None
+        timing_set = {"file": src, "kernel_hash": stored, "kernel_hash_now": kernel_source_hash(),
+                      "current": stored == kernel_source_hash(), "candidates": int(tr_t.shape[1])}
+        if not timing_set["current"]:
+            log("warning: the stored timing set was measured on other MTTKRP kernel sources")
+        if tr_t.shape[1] != len(tune.CANDIDATES):
+            raise RuntimeError("stored timing set has %d candidates, the autotuner %d: re-collect it with "
+                               "python -m paper_2102_10245_gb300.autotune" % (tr_t.shape[1], len(tune.CANDIDATES)))
     else:
         log("no stored timings: collecting the training set now")
         d = tune.collect(range(0, args.train_items), log=log)
@@ -580,8 +711,18 @@ def run_batched(args, rank, world, local):
     reg_rule = tune.regret(times, rule)
     log("regret: predictor %.3f / %.3f, rule %.3f / %.3f" % (reg_mlp + reg_rule))
 
+    def plan(sel):
+        """A batch whose items run the chosen candidates (variant and
+        segment count; the plan keeps the count it was built with)."""
+        for (at, n, _, _), k in zip(items, sel):
+            at.set_parts(n, tune.parts_for(at, tune.PARTS[int(k)]))
+        b = Batch(items, variants=[tune.VARIANTS[int(k)] for k in sel])
+        for at, n, _, _ in items:
+            at.set_parts(n, 0)
+        return b
+
     def batch_ms(sel):
-        b = Batch(items, variants=[tune.VARIANTS[p] for p in sel])
+        b = plan(sel)
         for _ in range(W):
             b.run()
         ms = _time_k(b.run, K, stream)
@@ -590,7 +731,7 @@ def run_batched(args, rank, world, local):
         return ms, info
     ms_rule, _ = batch_ms(rule)
     ms_best, _ = batch_ms(best)
-    bh = Batch(items, variants=[tune.VARIANTS[p] for p in picks])
+    bh = plan(picks)
     for _ in range(W):
         bh.run()
     torch.cuda.synchronize()
@@ -635,7 +776,7 @@ def run_batched(args, rank, world, local):
     achieved = tot_bytes / (ms / 1e3) / 1e9
     value = work / (ms / 1e3) / 1e9
     if rank != 0:
-        return
+        return None
     lab = tune.VARIANT_LABELS
     line = {
         "metric": METRIC, "value": value, "unit": "Gnnz/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -651,9 +792,11 @@ def run_batched(args, rank, world, local):
         "plain_fp32": {"ms": ms_plain, "gnnz_s": work / (ms_plain / 1e3) / 1e9,
                        "form": "one alto_mttkrp call per (tensor, mode), FP32 factors, built-in variant rule"},
         "speedup_vs_plain_fp32": ms_plain / ms,
+        "speedup_vs_fp32_batched": ms_b32_rule / ms,
         "context": {"fp32_batched_rule_ms": ms_b32_rule, "bf16_batched_rule_ms": ms_rule,
                     "bf16_batched_autotuned_ms": ms_best},
-        "predictor": {"train": src, "train_rows": int(len(tr_f)), "train_s": train_s, "infer_ms": infer_ms,
+        "predictor": {"train": src, "timing_set": timing_set, "train_rows": int(len(tr_f)), "train_s": train_s,
+                      "infer_ms": infer_ms,
                       "loss_first_last": [losses[0], losses[-1]],
                       "regret_total": reg_mlp[0], "regret_mean": reg_mlp[1],
                       "rule_regret_total": reg_rule[0], "rule_regret_mean": reg_rule[1],
@@ -671,7 +814,9 @@ def run_batched(args, rank, world, local):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_mttkrp_only(args):

@@ -60,7 +60,11 @@ typedef enum {
                              segment's output interval (Alg. 2, Temp_l), then
                              one atomic flush per touched row */
     ALTO_VAR_TEMP = 4     /* per-segment Temp in device memory plus the
-                             pull-based reduction of Alg. 2 */
+                             pull-based reduction of Alg. 2 */,
+    ALTO_VAR_GENERIC = 5  /* the kernel for any order and rank (no rank or
+                             order specialisation; one warp per segment,
+                             scalar atomics): the baseline of the
+                             rank-specialisation comparison (Sec. 4.5) */
 } alto_variant;
 
 #define ALTO_MAX_MODES 8
@@ -112,8 +116,10 @@ alto_status alto_options_init(alto_options *opt);
  *              (0-based) of width idx_bytes (4: uint32, 8: int64).  Each
  *              pointer may be device or host memory (detected); host data is
  *              copied to the device first.
- *   vals     : M values of type vdtype (ALTO_F64 or ALTO_F32), device or
- *              host memory.
+ *   vals     : M values of type vdtype (ALTO_F64, ALTO_F32 or ALTO_BF16),
+ *              device or host memory.  BF16 values are stored as BF16 (2 bytes
+ *              in the streamed format) and widened exactly to FP32 inside
+ *              the MTTKRP kernels; they go with FP32 or BF16 factors.
  *   opt      : options, or NULL for the defaults.
  * The inputs are read only and may be freed once the call returns.  The
  * call synchronises `stream` at its end and returns ALTO_ERANGE when an
@@ -131,7 +137,7 @@ alto_status alto_create(alto_t *out, int nmodes, const uint64_t *dims,
  *   factors : host array of N device pointers, factors[m] an I_m x rank
  *             matrix of fdtype; factors[mode] is not read (may be NULL).
  *   fdtype  : ALTO_F64 (values must be F64), ALTO_F32 or ALTO_BF16 (values
- *             must be F32; accumulation in FP32).
+ *             must be F32 or BF16; accumulation in FP32).
  *   out     : device I_mode x rank matrix, FP64 when fdtype is ALTO_F64 and
  *             FP32 otherwise; overwritten (the zero initialisation that
  *             Alg. 2 leaves implicit is done here).
@@ -258,13 +264,22 @@ alto_status alto_nn_adam(float *param, const float *grad, float *m, float *v,
 /* alto_set_variant -- override the MTTKRP variant of one mode. */
 alto_status alto_set_variant(alto_t t, int mode, int variant);
 
+/* alto_set_parts -- segment count used by mode `mode`'s ATOMIC and WARPAGG
+ * MTTKRPs (alto_mttkrp and batches planned afterwards): the line is cut into
+ * nparts equal-nnz segments, 8 consecutive segments per thread block
+ * (Sec. 3.2; L is a free parameter of the method).  0 restores the tensor's
+ * own L; values above nnz are clamped to nnz.  SMEM and TEMP always use the
+ * tensor's L (they read its per-segment intervals).  Errors: ALTO_EINVAL for
+ * a NULL handle, a bad mode or a negative count. */
+alto_status alto_set_parts(alto_t t, int mode, int64_t nparts);
+
 /* alto_resolve_variant -- the accumulation variant an alto_mttkrp call of
  * this mode, rank and factor dtype runs when it asks for `variant`
  * (ALTO_VAR_AUTO: the per-mode override, else the reuse rule of Sec. 3.3
  * adapted to the GPU: reuse M/I_n <= 4 -> ATOMIC, else WARPAGG; SMEM is
  * never chosen automatically).  Shapes without a specialised kernel report
  * ATOMIC (the generic kernel).  *out receives one of
- * ALTO_VAR_ATOMIC..ALTO_VAR_TEMP.  Host-only.  Errors: ALTO_EINVAL for a
+ * ALTO_VAR_ATOMIC..ALTO_VAR_GENERIC.  Host-only.  Errors: ALTO_EINVAL for a
  * NULL handle or output, a bad mode, rank, dtype or variant. */
 alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_dtype fdtype, int variant, int *out);
 

@@ -238,6 +238,38 @@ def mttkrp_threads(dims, idx, vals, factors, mode, threads):
     return out, used
 
 
+def mttkrp_sampled(dims, idx, vals, get_rows, mode, rows):
+    """Rows ``rows`` (sorted, distinct) of the mode-``mode`` MTTKRP by its
+    definition, without the full factor matrices: only the nonzeros whose
+    output row is in ``rows`` contribute, so they are kept, every input mode
+    is relabeled to the distinct rows those nonzeros touch, and ``mttkrp``
+    runs on that small problem (a relabeling of rows changes no sum).
+    ``get_rows(m, ids)`` returns the FP64 rows ``ids`` of factor m.  Returns a
+    len(rows) x R array in the order of ``rows``."""
+    rows = np.asarray(rows, dtype=np.int64)
+    out_idx = np.asarray(idx[mode]).astype(np.int64)
+    keep = np.isin(out_idx, rows)
+    sub_idx, sub_dims, fac = [], [], []
+    for m in range(len(dims)):
+        a = np.asarray(idx[m]).astype(np.int64)[keep]
+        if m == mode:
+            sub_idx.append(np.searchsorted(rows, a).astype(np.int64))
+            sub_dims.append(len(rows))
+            fac.append(None)
+        else:
+            u, inv = np.unique(a, return_inverse=True)
+            sub_idx.append(inv.astype(np.int64))
+            sub_dims.append(max(len(u), 1))
+            f = np.asarray(get_rows(m, u), dtype=np.float64)
+            if len(u) == 0:
+                f = np.zeros((1, f.shape[1] if f.ndim == 2 and f.shape[1] else 1))
+            fac.append(f)
+    v = np.asarray(vals, dtype=np.float64)[keep]
+    R = next(f.shape[1] for f in fac if f is not None)
+    fac[mode] = np.zeros((1, R))
+    return mttkrp(sub_dims, sub_idx, v, fac, mode)
+
+
 def reuse(dims, M):
     """Average fiber reuse per mode, M / I_n (Sec. 3.3)."""
     return [M / float(d) for d in dims]

@@ -17,8 +17,8 @@ ALTO_OK, ALTO_EINVAL, ALTO_ENOMEM, ALTO_ECUDA, ALTO_ETIMEOUT, ALTO_EOVERFLOW, AL
 STATUS_NAMES = {0: "ALTO_OK", 1: "ALTO_EINVAL", 2: "ALTO_ENOMEM", 3: "ALTO_ECUDA", 4: "ALTO_ETIMEOUT",
                 5: "ALTO_EOVERFLOW", 6: "ALTO_ENOTSPD", 7: "ALTO_ERANGE"}
 F64, F32, BF16 = 0, 1, 2
-VAR_AUTO, VAR_ATOMIC, VAR_WARPAGG, VAR_SMEM, VAR_TEMP = range(5)
-VARIANT_NAMES = {0: "auto", 1: "atomic", 2: "warpagg", 3: "smem", 4: "temp"}
+VAR_AUTO, VAR_ATOMIC, VAR_WARPAGG, VAR_SMEM, VAR_TEMP, VAR_GENERIC = range(6)
+VARIANT_NAMES = {0: "auto", 1: "atomic", 2: "warpagg", 3: "smem", 4: "temp", 5: "generic"}
 MAX_MODES = 8
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -59,6 +59,7 @@ def lib():
             "alto_get_stats": [P, P, P, P, P, P, P],
             "alto_export": [P, P, P, P, P, P],
             "alto_set_variant": [P, I, I],
+            "alto_set_parts": [P, I, I64],
             "alto_resolve_variant": [P, I, I, I, I, P],
             "alto_check": [P, P],
             "alto_destroy": [P],
@@ -240,9 +241,9 @@ class AltoTensor:
                 raise ValueError("index arrays must share one integer width and length nnz")
             if not a.is_contiguous():
                 raise ValueError("index arrays must be contiguous")
-        if vals.dtype not in (torch.float32, torch.float64) or not vals.is_contiguous():
-            raise ValueError("values must be contiguous float32 or float64")
-        self.vdtype = F64 if vals.dtype == torch.float64 else F32
+        if vals.dtype not in (torch.float32, torch.float64, torch.bfloat16) or not vals.is_contiguous():
+            raise ValueError("values must be contiguous float32, float64 or bfloat16")
+        self.vdtype = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[vals.dtype]
         opt = Options()
         lib().alto_options_init(ctypes.byref(opt))
         opt.key_bits = key_bits
@@ -307,11 +308,13 @@ class AltoTensor:
         M, L = st["nnz"], st["nparts"]
         keys = np.zeros((M, lay["key_words"]), dtype=np.uint64)
         perm = np.zeros(M, dtype=np.uint32)
-        vals = np.zeros(M, dtype=np.float64 if self.vdtype == F64 else np.float32)
+        vals = np.zeros(M, dtype={F64: np.float64, F32: np.float32, BF16: np.uint16}[self.vdtype])
         bounds = np.zeros(L + 1, dtype=np.int64)
         ivl = np.zeros((L, self.N, 2), dtype=np.uint32)
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
         _check(lib().alto_export(self._h, vp(keys), vp(perm), vp(vals), vp(bounds), vp(ivl)))
+        if self.vdtype == BF16:  # BF16 bits -> the exact FP32 values
+            vals = (vals.astype(np.uint32) << 16).view(np.float32)
         return dict(keys=keys, perm=perm, vals=vals, bounds=bounds, intervals=ivl)
 
     def mode_stats(self, mode):
@@ -328,6 +331,11 @@ class AltoTensor:
 
     def set_variant(self, mode, variant):
         _check(lib().alto_set_variant(self._h, mode, int(variant)))
+
+    def set_parts(self, mode, nparts):
+        """Segment count of this mode's ATOMIC / WARPAGG MTTKRPs (0: the
+        tensor's own L)."""
+        _check(lib().alto_set_parts(self._h, mode, int(nparts)))
 
     def resolve_variant(self, mode, rank, fdtype=F32, variant=0):
         """The variant an MTTKRP of this mode and rank runs for ``variant``."""

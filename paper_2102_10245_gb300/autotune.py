@@ -7,7 +7,8 @@ compares a set of picks with the autotuned ones.
 The accumulation strategies are the ones of Sec. 3.3 (direct atomic updates
 for low fiber reuse, buffered accumulation for high reuse) in their GPU
 forms: ATOMIC, WARPAGG (register runs + replicated hot rows) and SMEM
-(shared-memory Temp over the unit's output interval).  The library's own
+(shared-memory Temp over the unit's output interval), each with a choice of
+the segment count L of Sec. 3.2.  The library's own
 rule (alto_resolve_variant with AUTO) is the method without the predictor.
 """
 import math
@@ -18,8 +19,33 @@ import torch
 from .alto import BF16, F32, F64, VAR_ATOMIC, VAR_SMEM, VAR_WARPAGG, AltoTensor
 from .mlp import MLP
 
-VARIANTS = (VAR_ATOMIC, VAR_WARPAGG, VAR_SMEM)
-VARIANT_LABELS = ("atomic", "warpagg", "smem")
+# The autotuner's choices for one (tensor, mode): accumulation variant x
+# segment count of the ALTO line (Sec. 3.2 leaves L free; the GPU kernels use
+# it to cut the line into thread-block units), the count as a factor of the
+# tensor's own L (alto_set_parts; SMEM keeps L, it reads the segments'
+# intervals).  VARIANTS / PARTS are the two columns.
+CANDIDATES = ((VAR_ATOMIC, 1.0), (VAR_WARPAGG, 1.0), (VAR_SMEM, 1.0),
+              (VAR_ATOMIC, 0.25), (VAR_WARPAGG, 0.25), (VAR_ATOMIC, 4.0), (VAR_WARPAGG, 4.0))
+VARIANTS = tuple(v for v, _ in CANDIDATES)
+PARTS = tuple(f for _, f in CANDIDATES)
+_NAMES = {VAR_ATOMIC: "atomic", VAR_WARPAGG: "warpagg", VAR_SMEM: "smem"}
+VARIANT_LABELS = tuple("%s/L%s" % (_NAMES[v], "" if f == 1.0 else ("*%g" % f)) for v, f in CANDIDATES)
+
+
+def parts_for(at, factor):
+    """Segment count of candidate factor ``factor`` on tensor ``at`` (0 for the
+    tensor's own L)."""
+    if factor == 1.0:
+        return 0
+    L = int(at.stats()["nparts"])
+    return max(1, min(int(round(L * factor)), max(at.nnz, 1)))
+
+
+def apply(at, mode, k):
+    """Set mode ``mode`` of ``at`` to candidate ``k`` (variant and segment
+    count), for alto_mttkrp calls and batches planned afterwards."""
+    at.set_variant(mode, VARIANTS[k])
+    at.set_parts(mode, parts_for(at, PARTS[k]))
 
 FEATURES = (
     "order", "log2_len", "log2_nnz", "log2_reuse", "log2_rank", "distinct_frac", "hot_share",
@@ -53,14 +79,16 @@ def features(at, mode, rank, fdtype=BF16):
     ], dtype=np.float64)
 
 
-def time_variants(at, mode, factors, out, variants=VARIANTS, target_ms=0.25, max_reps=64, trials=2):
-    """Device time (ms) of one MTTKRP call per variant.  Each variant's calls
-    are captured ``reps`` times into one CUDA graph, so launch overhead of
-    the host does not enter; the best of ``trials`` replays counts."""
+def time_variants(at, mode, factors, out, candidates=None, target_ms=0.25, max_reps=64, trials=2):
+    """Device time (ms) of one MTTKRP call per candidate (indices into
+    CANDIDATES; all by default).  Each candidate's calls are captured ``reps``
+    times into one CUDA graph, so launch overhead of the host does not enter;
+    the best of ``trials`` replays counts.  Leaves the mode on the automatic
+    variant and the tensor's own L."""
     res = []
     stream = torch.cuda.Stream()
-    for v in variants:
-        at.set_variant(mode, v)
+    for k in (range(len(CANDIDATES)) if candidates is None else candidates):
+        apply(at, mode, k)
         at.mttkrp(mode, factors, out, stream=stream)  # allocates the hot-row replicas
         stream.synchronize()
         # estimate one call to size the graph
@@ -91,13 +119,15 @@ def time_variants(at, mode, factors, out, variants=VARIANTS, target_ms=0.25, max
         del g
         res.append(best)
     at.set_variant(mode, 0)
+    at.set_parts(mode, 0)
     return np.array(res)
 
 
 def rule_pick(at, mode, rank, fdtype=BF16):
-    """Index into VARIANTS of the library's built-in choice."""
+    """Index into CANDIDATES of the library's built-in choice (its variant
+    with the tensor's own L)."""
     v = at.resolve_variant(mode, rank, fdtype)
-    return VARIANTS.index(v) if v in VARIANTS else VARIANTS.index(VAR_WARPAGG)
+    return CANDIDATES.index((v, 1.0)) if (v, 1.0) in CANDIDATES else CANDIDATES.index((VAR_WARPAGG, 1.0))
 
 
 def make_item(cfg, device="cuda", fdtype=BF16):
@@ -135,7 +165,7 @@ def collect(seeds, device="cuda", fdtype=BF16, log=None):
             log("collected %d / %d tensors" % (k + 1, len(seeds)))
     return dict(features=np.array(feats), times=np.array(times), rule=np.array(rule, np.int64),
                 meta=np.array(meta, np.int64), feature_names=np.array(FEATURES),
-                variants=np.array(VARIANTS, np.int64))
+                variants=np.array(VARIANTS, np.int64), parts=np.array(PARTS, np.float64))
 
 
 def regret(times, picks):
@@ -180,7 +210,7 @@ class Predictor:
         if weight is not None:
             w = np.repeat(np.asarray(weight, np.float64)[:, None], Y.shape[1], axis=1)
             mask = torch.from_numpy((w / w.mean()).astype(np.float32)).to(self.device)
-        self.net = MLP((feats.shape[1],) + self.hidden + (len(VARIANTS),), seed=self.seed, device=self.device)
+        self.net = MLP((feats.shape[1],) + self.hidden + (Y.shape[1],), seed=self.seed, device=self.device)
         return self.net.fit(X, Y, mask=mask, epochs=epochs, lr=lr)
 
     def scores(self, feats):
@@ -190,13 +220,14 @@ class Predictor:
         return self.scores(feats).argmin(axis=1)
 
     def configure(self, at, rank, fdtype=BF16):
-        """Set every mode of ``at`` to the predicted variant (alto_set_variant),
-        so plain alto_mttkrp / alto_cpals calls use it; returns the variants."""
+        """Set every mode of ``at`` to the predicted candidate (variant and
+        segment count), so plain alto_mttkrp / alto_cpals calls use it;
+        returns the variants."""
         feats = np.array([features(at, n, rank, fdtype) for n in range(at.N)])
-        picks = [VARIANTS[int(p)] for p in self.pick(feats)]
-        for n, v in enumerate(picks):
-            at.set_variant(n, v)
-        return picks
+        picks = [int(p) for p in self.pick(feats)]
+        for n, k in enumerate(picks):
+            apply(at, n, k)
+        return [VARIANTS[k] for k in picks]
 
     def save(self, path):
         arrays = {"mu": self.mu, "sd": self.sd, "hidden": np.array(self.hidden)}
@@ -248,8 +279,10 @@ def main(argv=None):
     a = ap.parse_args(argv)
     log = lambda m: print("[autotune %.0fs] %s" % (time.time() - t0, m), file=sys.stderr, flush=True)  # noqa: E731
     t0 = time.time()
+    from .build import kernel_source_hash
     dev_name = torch.cuda.get_device_name()
-    parts = {"device": np.array(dev_name)}
+    parts = {"device": np.array(dev_name), "kernel_hash": np.array(kernel_source_hash()),
+             "candidates": np.array(VARIANT_LABELS)}
     for name, text in (("heldout", a.heldout), ("train", a.train)):
         seeds = _seed_range(text)
         chunks = []
@@ -257,7 +290,7 @@ def main(argv=None):
             chunks.append(collect(seeds[c0:c0 + 250], log=log))
             for k in chunks[0]:
                 vals = [c[k] for c in chunks]
-                parts["%s_%s" % (name, k)] = vals[0] if k in ("feature_names", "variants") else np.concatenate(vals)
+                parts["%s_%s" % (name, k)] = vals[0] if k in ("feature_names", "variants", "parts") else np.concatenate(vals)
             np.savez_compressed(a.out, **parts)
             log("%s: %d / %d tensors saved" % (name, min(c0 + 250, len(seeds)), len(seeds)))
 

@@ -41,6 +41,17 @@ def _compile(src, force, hdr_time):
     return obj
 
 
+def kernel_source_hash():
+    """Hash of the MTTKRP kernel sources: recorded measurements (ncu traffic,
+    the autotuner's timing set) are only used while it matches."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(SRC, "mttkrp*")) + [os.path.join(SRC, "common.cuh")])
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def build(force=False, jobs=None):
     """Compile and link; returns the path of libalto.so."""
     os.makedirs(OUT, exist_ok=True)

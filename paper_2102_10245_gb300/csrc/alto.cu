@@ -208,7 +208,8 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
   if (nnz < 0 || nnz >= (int64_t(1) << 32)) return fail(ALTO_EINVAL, "nnz %lld outside [0, 2^32)", (long long)nnz);
   if (nnz > 0 && (idx == nullptr || vals == nullptr)) return fail(ALTO_EINVAL, "null indices or values");
   if (idx_bytes != 4 && idx_bytes != 8) return fail(ALTO_EINVAL, "idx_bytes must be 4 or 8");
-  if (vdtype != ALTO_F64 && vdtype != ALTO_F32) return fail(ALTO_EINVAL, "values must be F64 or F32");
+  if (vdtype != ALTO_F64 && vdtype != ALTO_F32 && vdtype != ALTO_BF16)
+    return fail(ALTO_EINVAL, "values must be F64, F32 or BF16");
   alto_options o;
   alto_options_init(&o);
   if (opt != nullptr) o = *opt;
@@ -221,7 +222,7 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     for (int n = 0; n < nmodes; ++n)
       if (idx[n] == nullptr) return fail(ALTO_EINVAL, "index array %d is null", n);
   for (int n = 0; n < nmodes; ++n)
-    if (o.variant[n] < ALTO_VAR_AUTO || o.variant[n] > ALTO_VAR_TEMP)
+    if (o.variant[n] < ALTO_VAR_AUTO || o.variant[n] > ALTO_VAR_GENERIC)
       return fail(ALTO_EINVAL, "bad variant %d for mode %d", o.variant[n], n);
 
   alto_tensor_s* t = new (std::nothrow) alto_tensor_s();
@@ -234,7 +235,7 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int N = nmodes;
   const int KW = lay.KW;
-  const size_t vb = vdtype == ALTO_F64 ? 8 : 4;
+  const size_t vb = vdtype == ALTO_F64 ? 8 : (vdtype == ALTO_F32 ? 4 : 2);
   // temporaries
   std::vector<void*> staged;
   uint64_t* keys_alt = nullptr;
@@ -497,7 +498,7 @@ alto_status alto_export(alto_t t, uint64_t* keys, uint32_t* perm, void* vals, in
   if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
   alto_status st = ALTO_OK;
   const size_t M = static_cast<size_t>(t->M);
-  const size_t vb = t->vdtype == ALTO_F64 ? 8 : 4;
+  const size_t vb = t->vdtype == ALTO_F64 ? 8 : (t->vdtype == ALTO_F32 ? 4 : 2);
   if (keys && M) CK(cudaMemcpy(keys, t->keys, sizeof(uint64_t) * t->lay.KW * M, cudaMemcpyDeviceToHost));
   if (perm && M) CK(cudaMemcpy(perm, t->perm, sizeof(uint32_t) * M, cudaMemcpyDeviceToHost));
   if (vals && M) CK(cudaMemcpy(vals, t->vals, vb * M, cudaMemcpyDeviceToHost));
@@ -545,8 +546,16 @@ alto_status alto_get_unit_fit(alto_t t, int mode, uint64_t rows, double* frac) {
 alto_status alto_set_variant(alto_t t, int mode, int variant) {
   if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
   if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
-  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_GENERIC) return fail(ALTO_EINVAL, "bad variant %d", variant);
   t->variant[mode] = variant;
+  return ALTO_OK;
+}
+
+alto_status alto_set_parts(alto_t t, int mode, int64_t nparts) {
+  if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
+  if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
+  if (nparts < 0) return fail(ALTO_EINVAL, "negative segment count %lld", static_cast<long long>(nparts));
+  t->mode_parts[mode] = nparts;
   return ALTO_OK;
 }
 

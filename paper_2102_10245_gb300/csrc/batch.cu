@@ -28,6 +28,7 @@ alto_status check_mttkrp_args(const alto_tensor_s* t, int mode, const void* cons
 int resolve_variant(const alto_tensor_s* t, int mode, int R, size_t osz, int variant);
 void fill_launch(const alto_tensor_s* t, int mode, const void* const* factors, int R, void* out,
                  MttkrpLaunch* l);
+int64_t mttkrp_parts(const alto_tensor_s* t, int mode, int variant);
 size_t smem_temp_bytes(const alto_tensor_s* t, int mode, int R, size_t osz, int* rows_out);
 cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors, int R,
                           alto_dtype fdtype, void* out, int variant, size_t osz, cudaStream_t s);
@@ -121,7 +122,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     }
     int v = resolve_variant(t, mode, R, osz, variants ? variants[i] : ALTO_VAR_AUTO);
     if (v == ALTO_VAR_TEMP) v = ALTO_VAR_WARPAGG;  // the per-unit device Temp is not batched
-    if (!mttkrp_specialised(t->lay.N, R)) {
+    if (!mttkrp_specialised(t->lay.N, R) || v == ALTO_VAR_GENERIC) {
       single.push_back(i);
       continue;
     }
@@ -135,6 +136,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
                static_cast<double>(z.bytes);
     MttkrpLaunch l{};
     fill_launch(t, mode, factors[i], R, outs[i], &l);
+    l.args.L = mttkrp_parts(t, mode, v);
     size_t smem = 0;
     if (v == ALTO_VAR_SMEM) {
       int rows = 0;
@@ -252,8 +254,8 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
   }
   for (size_t k = 0; e == cudaSuccess && k < single.size(); ++k) {
     const int i = single[k];
-    // no specialised kernel: the generic one (which ignores the variant)
-    e = mttkrp_launch(tensors[i], modes[i], factors[i], ranks[i], fdtype, outs[i], ALTO_VAR_ATOMIC, osz,
+    // no specialised kernel (or the generic one requested): the generic kernel
+    e = mttkrp_launch(tensors[i], modes[i], factors[i], ranks[i], fdtype, outs[i], ALTO_VAR_GENERIC, osz,
                       fs[(dev_groups.size() + k) % branches]);
   }
   for (int k = 0; e == cudaSuccess && k < branches; ++k) {

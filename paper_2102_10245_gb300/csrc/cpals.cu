@@ -781,8 +781,8 @@ alto_status run_cpals(alto_tensor_s* t, int R, int iters, void* const* factors, 
     if (factors[m] == nullptr) return fail(ALTO_EINVAL, "factor %d is null", m);
   if (fdtype == ALTO_F64 && t->vdtype != ALTO_F64)
     return fail(ALTO_EINVAL, "FP64 factors need FP64 values");
-  if (fdtype != ALTO_F64 && t->vdtype != ALTO_F32)
-    return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 values");
+  if (fdtype != ALTO_F64 && t->vdtype != ALTO_F32 && t->vdtype != ALTO_BF16)
+    return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 or BF16 values");
   CpalsWork& w = t->cp;
   const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
   uint64_t maxI = 0;

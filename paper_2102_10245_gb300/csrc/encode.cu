@@ -70,6 +70,12 @@ __global__ void __launch_bounds__(256) permute_kernel(const T* __restrict__ src,
     dst[x] = src[perm[x]];
 }
 
+__device__ __forceinline__ double value_f64(double v) { return v; }
+__device__ __forceinline__ double value_f64(float v) { return static_cast<double>(v); }
+__device__ __forceinline__ double value_f64(uint16_t b) {  // a BF16 value's bits
+  return static_cast<double>(__uint_as_float(static_cast<uint32_t>(b) << 16));
+}
+
 // ||X||^2 where X sums duplicate coordinates: over the ordered keys, every
 // run of equal keys contributes (sum of its values)^2.
 template <typename T, int KW>
@@ -84,13 +90,13 @@ __global__ void __launch_bounds__(256) sumsq_kernel(const uint64_t* __restrict__
       for (int w = 0; w < KW; ++w) start |= keys[x * KW + w] != keys[(x - 1) * KW + w];
     }
     if (!start) continue;
-    double run = static_cast<double>(v[x]);
+    double run = value_f64(v[x]);
     for (int64_t y = x + 1; y < M; ++y) {
       bool same = true;
 #pragma unroll
       for (int w = 0; w < KW; ++w) same &= keys[y * KW + w] == keys[x * KW + w];
       if (!same) break;
-      run += static_cast<double>(v[y]);
+      run += value_f64(v[y]);
     }
     s += run * run;
   }
@@ -311,9 +317,12 @@ cudaError_t launch_permute(const void* src, void* dst, const uint32_t* perm, int
   if (elem_bytes == 8)
     permute_kernel<uint64_t><<<g, 256, 0, s>>>(static_cast<const uint64_t*>(src),
                                                static_cast<uint64_t*>(dst), perm, M);
-  else
+  else if (elem_bytes == 4)
     permute_kernel<uint32_t><<<g, 256, 0, s>>>(static_cast<const uint32_t*>(src),
                                                static_cast<uint32_t*>(dst), perm, M);
+  else
+    permute_kernel<uint16_t><<<g, 256, 0, s>>>(static_cast<const uint16_t*>(src),
+                                               static_cast<uint16_t*>(dst), perm, M);
   note_launch();
   return cudaGetLastError();
 }
@@ -328,11 +337,16 @@ cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dt
       sumsq_kernel<double, 1><<<g, 256, 0, s>>>(keys, static_cast<const double*>(vals), M, out);
     else
       sumsq_kernel<double, 2><<<g, 256, 0, s>>>(keys, static_cast<const double*>(vals), M, out);
-  } else {
+  } else if (vd == ALTO_F32) {
     if (KW == 1)
       sumsq_kernel<float, 1><<<g, 256, 0, s>>>(keys, static_cast<const float*>(vals), M, out);
     else
       sumsq_kernel<float, 2><<<g, 256, 0, s>>>(keys, static_cast<const float*>(vals), M, out);
+  } else {
+    if (KW == 1)
+      sumsq_kernel<uint16_t, 1><<<g, 256, 0, s>>>(keys, static_cast<const uint16_t*>(vals), M, out);
+    else
+      sumsq_kernel<uint16_t, 2><<<g, 256, 0, s>>>(keys, static_cast<const uint16_t*>(vals), M, out);
   }
   note_launch();
   return cudaGetLastError();

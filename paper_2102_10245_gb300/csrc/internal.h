@@ -87,6 +87,7 @@ struct alto_tensor_s {
   uint64_t max_ivl[alto::kMaxModes] = {};
   double reuse[alto::kMaxModes] = {};
   int variant[alto::kMaxModes] = {};
+  int64_t mode_parts[alto::kMaxModes] = {};  // per-mode segment count of ATOMIC / WARPAGG (0: L)
   double normX2 = 0.0;
   // Thread-block units (8 consecutive segments): union of their intervals
   // per mode, kept on the host (unit_lo / unit_hi) and as sorted widths.

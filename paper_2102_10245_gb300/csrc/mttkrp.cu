@@ -59,11 +59,12 @@ alto_status check_mttkrp_args(const alto_tensor_s* t, int mode, const void* cons
   if (fdtype == ALTO_F64) {
     if (t->vdtype != ALTO_F64) return fail(ALTO_EINVAL, "FP64 factors need FP64 values");
   } else if (fdtype == ALTO_F32 || fdtype == ALTO_BF16) {
-    if (t->vdtype != ALTO_F32) return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 values");
+    if (t->vdtype != ALTO_F32 && t->vdtype != ALTO_BF16)
+      return fail(ALTO_EINVAL, "FP32/BF16 factors need FP32 or BF16 values");
   } else {
     return fail(ALTO_EINVAL, "bad factor dtype %d", static_cast<int>(fdtype));
   }
-  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_GENERIC) return fail(ALTO_EINVAL, "bad variant %d", variant);
   return ALTO_OK;
 }
 
@@ -73,6 +74,16 @@ int resolve_variant(const alto_tensor_s* t, int mode, int R, size_t osz, int var
   int v = variant != ALTO_VAR_AUTO ? variant : t->variant[mode];
   if (v == ALTO_VAR_AUTO) v = auto_variant(t, mode, R, osz);
   return v;
+}
+
+// Segment count of an MTTKRP: the per-mode override for the ATOMIC and
+// WARPAGG policies (they use the segments only to cut the line into
+// thread-block units), else the tensor's L (SMEM and TEMP read the segments'
+// intervals).  At most M, at least 1.
+int64_t mttkrp_parts(const alto_tensor_s* t, int mode, int variant) {
+  const int64_t p = t->mode_parts[mode];
+  if (p <= 0 || !(variant == ALTO_VAR_ATOMIC || variant == ALTO_VAR_WARPAGG)) return t->L;
+  return p < t->M ? p : (t->M > 0 ? t->M : 1);
 }
 
 // Arguments common to every variant.
@@ -88,6 +99,7 @@ void fill_launch(const alto_tensor_s* t, int mode, const void* const* factors, i
   make_decode(lay, slot_mode, &l->args.dp);
   l->args.keys = t->keys;
   l->args.vals = t->vals;
+  l->args.vbf16 = t->vdtype == ALTO_BF16 ? 1 : 0;
   l->args.M = t->M;
   l->args.L = t->L;
   for (int sl = 0; sl < N; ++sl) l->args.f[sl] = factors[slot_mode[sl]];
@@ -132,8 +144,14 @@ cudaError_t mttkrp_launch(alto_tensor_s* t, int mode, const void* const* factors
   MttkrpLaunch l{};
   fill_launch(t, mode, factors, R, out, &l);
   if (v == ALTO_VAR_TEMP) return launch_temp_variant(t, l, fdtype, osz, s);
+  if (v == ALTO_VAR_GENERIC) {  // the rank- and order-generic kernel on request
+    l.variant = v;
+    l.generic = true;
+    return mttkrp_dispatch(l, fdtype, s);
+  }
   if (!mttkrp_specialised(N, R)) v = ALTO_VAR_ATOMIC;  // the generic kernel
   l.variant = v;
+  l.args.L = mttkrp_parts(t, mode, v);
   const size_t fsz = fdtype == ALTO_F64 ? 8 : (fdtype == ALTO_F32 ? 4 : 2);
   l.fused = (v == ALTO_VAR_ATOMIC || v == ALTO_VAR_WARPAGG) && mttkrp_specialised(N, R) &&
             fused_ok(N, R, fsz, l.args.f, out, osz, lay.dims[mode]);
@@ -189,12 +207,12 @@ extern "C" alto_status alto_resolve_variant(alto_t t, int mode, int rank, alto_d
   if (t == nullptr || out == nullptr) return fail(ALTO_EINVAL, "null argument");
   if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "mode %d outside [0, %d)", mode, t->lay.N);
   if (rank < 1) return fail(ALTO_EINVAL, "rank %d < 1", rank);
-  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_TEMP) return fail(ALTO_EINVAL, "bad variant %d", variant);
+  if (variant < ALTO_VAR_AUTO || variant > ALTO_VAR_GENERIC) return fail(ALTO_EINVAL, "bad variant %d", variant);
   if (fdtype != ALTO_F64 && fdtype != ALTO_F32 && fdtype != ALTO_BF16)
     return fail(ALTO_EINVAL, "bad factor dtype %d", static_cast<int>(fdtype));
   const size_t osz = fdtype == ALTO_F64 ? 8 : 4;
   int v = resolve_variant(t, mode, rank, osz, variant);
-  if (v != ALTO_VAR_TEMP && !mttkrp_specialised(t->lay.N, rank)) v = ALTO_VAR_ATOMIC;
+  if (v != ALTO_VAR_TEMP && v != ALTO_VAR_GENERIC && !mttkrp_specialised(t->lay.N, rank)) v = ALTO_VAR_ATOMIC;
   *out = v;
   return ALTO_OK;
 }

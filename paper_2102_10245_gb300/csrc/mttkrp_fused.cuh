@@ -365,7 +365,7 @@ __device__ __forceinline__ void process_unit_fused(const MttkrpArgs& a, int64_t 
   auto load = [&](int64_t x, KeyT<KW>& k, VT& v) {
     if (x + lane < ue) {
       k = load_key<KW>(a.keys, x + lane);
-      v = __ldcs(static_cast<const VT*>(a.vals) + x + lane);
+      v = load_value<VT>(a, x + lane);
     }
   };
 

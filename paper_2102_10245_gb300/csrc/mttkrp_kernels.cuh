@@ -212,7 +212,7 @@ __device__ __forceinline__ void red_vec(double* out, const double* v) {
 
 struct MttkrpArgs {
   const uint64_t* keys;
-  const void* vals;          // FP64 when the factors are FP64, else FP32
+  const void* vals;          // FP64 when the factors are FP64, else FP32 or BF16 (vbf16)
   int64_t M;
   int64_t L;                 // line segments
   const void* f[kMaxModes];  // factor of each decode slot; slot N-1 is the output mode
@@ -229,6 +229,7 @@ struct MttkrpArgs {
   int hot_bits;              // WARPAGG: log2 of the hash table size
   int hot_key_bit;           // WARPAGG: key bit flagging hot output rows, or -1
   void* hot_rep;             // WARPAGG: kHotReplicas x hot_n x R accumulators
+  int vbf16;                 // values stored as BF16 (FP32 / BF16 factors only)
   DecodeParams dp;
 };
 
@@ -259,6 +260,22 @@ constexpr int kThreads = kWarps * 32;
 // the L1 data path, not the latency of single gathers, bounds the kernel.
 constexpr int kGatherDepth = 1;
 static_assert(sizeof(MttkrpArgs) % 4 == 0, "MttkrpArgs is copied as 32-bit words");
+
+// Value x of the tensor as the accumulation's value type: FP64 values for
+// FP64 factors; FP32 or BF16 values (widened exactly) otherwise.  Streamed
+// once, so loaded with the evict-first hint.
+template <typename VT>
+__device__ __forceinline__ VT load_value(const MttkrpArgs& a, int64_t x) {
+  if constexpr (std::is_same_v<VT, double>) {
+    return __ldcs(static_cast<const double*>(a.vals) + x);
+  } else {
+    if (a.vbf16) {
+      const unsigned short b = __ldcs(static_cast<const unsigned short*>(a.vals) + x);
+      return __uint_as_float(static_cast<uint32_t>(b) << 16);
+    }
+    return __ldcs(static_cast<const float*>(a.vals) + x);
+  }
+}
 
 // staged tuple: N indices and the value, padded to 16-byte words
 template <int N, typename VT>
@@ -535,7 +552,7 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
   VT vn = VT(0);
   if (base + lane < ue) {
     kn = load_key<KW>(a.keys, base + lane);
-    vn = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
+    vn = load_value<VT>(a, base + lane);
   }
   for (; base < ue; base += kWarps * 32) {
     const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
@@ -545,7 +562,7 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
     const int64_t nb = base + kWarps * 32;
     if (nb + lane < ue) {  // prefetch the warp's next chunk
       kn = load_key<KW>(a.keys, nb + lane);
-      vn = __ldcs(static_cast<const VT*>(a.vals) + nb + lane);
+      vn = load_value<VT>(a, nb + lane);
     }
     uint32_t id[N];
 #pragma unroll
@@ -825,7 +842,7 @@ __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_c
       if (lane < cnt) {
         const KeyT<KW> k = load_key<KW>(a.keys, base + lane);
         for (int s = 0; s < Nm; ++s) s_idx[warp][s][lane] = extract<KW>(k, a.dp, s);
-        s_val[warp][lane] = __ldcs(static_cast<const VT*>(a.vals) + base + lane);
+        s_val[warp][lane] = load_value<VT>(a, base + lane);
       }
       __syncwarp();
       for (int p = 0; p < cnt; ++p) {
@@ -854,6 +871,7 @@ struct MttkrpLaunch {
   int sms;       // SM count of the device
   size_t smem_dyn;
   bool fused;    // ATOMIC / WARPAGG through the fused body
+  bool generic;  // the rank- and order-generic kernel whatever the shape
 };
 
 cudaError_t mttkrp_dispatch_f32_k1(const MttkrpLaunch& l, cudaStream_t s);
@@ -984,6 +1002,7 @@ template <typename FT, int KW>
 cudaError_t mttkrp_dispatch_typed(const MttkrpLaunch& l, cudaStream_t s) {
   const MttkrpArgs& a = l.args;
   const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
+  if (l.generic) return launch_persistent(mttkrp_generic_kernel<KW, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
 #define ALTO_LAUNCH_NR(NN, RR)                                                                           \
   do {                                                                                                   \
     switch (l.variant) {                                                                                 \

@@ -80,7 +80,7 @@ def test_live_timing_features_and_rule(alto_lib):
         # the timing leaves the tensor on the automatic choice and the result exact
         assert at.stats()["variant"][n] == 0
         ref = at.mttkrp(n, factors)
-        at.set_variant(n, tune.VARIANTS[int(np.argmin(t))])
+        tune.apply(at, n, int(np.argmin(t)))
         got = at.mttkrp(n, factors)
         torch.cuda.synchronize()
         assert torch.allclose(got, ref, rtol=1e-4, atol=1e-4 * float(ref.abs().max()))

@@ -135,3 +135,70 @@ def test_dtype_mismatch_rejected():
     assert e.value.status == 1
     with pytest.raises(AltoError):
         at.set_variant(5, 1)
+
+
+def _bf16_values(vals):
+    """BF16-rounded copy of FP32 values (torch bf16 on the GPU) and their
+    exact FP64 values."""
+    t = torch.from_numpy(np.ascontiguousarray(vals, dtype=np.float32)).to(torch.bfloat16)
+    return t.cuda(), t.to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("variant", VARIANTS + [5])
+@pytest.mark.parametrize("fdt", ["f32", "bf16"])
+def test_bf16_values(variant, fdt):
+    """Values stored as BF16 (2-byte value stream), FP32 accumulation: within
+    1e-5 of the oracle on the BF16-rounded values (and rounded factors), 1e-2
+    of the oracle on the FP32 values; the exported values are the rounded
+    ones in ALTO order."""
+    from paper_2102_10245_gb300 import AltoTensor
+    from helpers import dev_idx
+    cfg = synth.scaled("zipf3d-4Mx4Mx30k", nnz=300_000)
+    dims, idx, vals = synth.tensor(cfg)
+    U = synth.factors(cfg)
+    vb, vr = _bf16_values(vals)
+    at = AltoTensor(dims, dev_idx(idx), vb)
+    if fdt == "bf16":
+        pairs = [to_bf16_exact(u) for u in U]
+        Ud, Ur = [p[0] for p in pairs], [p[1] for p in pairs]
+    else:
+        Ud, Ur = [dev(u) for u in U], [u.astype(np.float64) for u in U]
+    ex = at.export()
+    assert np.array_equal(ex["vals"].astype(np.float64), vr[ex["perm"]])
+    for n in range(len(dims)):
+        at.set_variant(n, variant)
+        got = at.mttkrp(n, Ud).cpu().numpy()
+        e_round = rel_err(got, oracle.mttkrp(dims, idx, vr, Ur, n))
+        e_full = rel_err(got, oracle.mttkrp(dims, idx, vals, U, n))
+        print("bf16 values, %s factors, mode %d variant %d: %.3e vs rounded, %.3e vs fp32" % (fdt, n, variant,
+                                                                                             e_round, e_full))
+        assert e_round <= 1e-5 and e_full <= 1e-2
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_segment_count_override(variant):
+    """alto_set_parts: any segment count (coarser, finer, one segment, more
+    than nnz) gives the same MTTKRP for ATOMIC and WARPAGG; 0 restores L."""
+    cfg = synth.scaled("clustered4d-12kx60kx5Mx100", nnz=200_000)
+    dims, idx, vals = synth.tensor(cfg)
+    U = synth.factors(cfg)
+    at = make(dims, idx, vals)
+    Ud = [dev(u) for u in U]
+    L = at.stats()["nparts"]
+    for parts in (max(1, L // 4), L * 4, 1, 10 * len(vals), 0):
+        for n in range(len(dims)):
+            at.set_variant(n, variant)
+            at.set_parts(n, parts)
+            got = at.mttkrp(n, Ud).cpu().numpy()
+            err = rel_err(got, oracle.mttkrp(dims, idx, vals, U, n))
+            assert err <= 1e-5, (parts, n, err)
+
+
+def test_generic_variant_forced():
+    """ALTO_VAR_GENERIC runs the runtime-rank kernel on a specialised shape."""
+    cfg = synth.scaled("zipf3d-4Mx4Mx30k", nnz=100_000)
+    dims, idx, vals = synth.tensor(cfg)
+    U = synth.factors(cfg)
+    at = make(dims, idx, vals)
+    run_all_modes(at, dims, idx, vals, U, 5, 1e-5, "generic forced")
+    assert at.resolve_variant(0, 32, 1, 5) == 5

@@ -472,3 +472,19 @@ def test_threaded_mttkrp_is_bit_identical():
         b, used = oracle.mttkrp_threads(dims, idx, vals, U, n, 4)
         assert used >= 1
         assert np.array_equal(a, b)
+
+
+def test_sampled_mttkrp_equals_full_rows():
+    """Sampled-row MTTKRP (nonzeros filtered by output row, input rows
+    relabeled) gives exactly the rows of the full oracle MTTKRP."""
+    import synth
+    cfg = synth.scaled("zipf3d-4Mx4Mx30k", nnz=40_000)
+    cfg["dims"] = (30_000, 20_000, 3000)
+    dims, idx, vals = synth.tensor(cfg)
+    rng = np.random.default_rng(9)
+    U = [rng.standard_normal((d, 8)) for d in dims]
+    for n in range(3):
+        full = oracle.mttkrp(dims, idx, vals, U, n)
+        rows = np.sort(rng.choice(dims[n], size=500, replace=False))
+        got = oracle.mttkrp_sampled(dims, idx, vals, lambda m, ids: U[m][ids], n, rows)
+        assert np.array_equal(got, full[rows])

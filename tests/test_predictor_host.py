@@ -39,7 +39,7 @@ def test_learning_setup_beats_rule_on_heldout():
     Xs = (X - mu) / sd
     Y = targets(T)
     rng = np.random.default_rng(0)
-    sizes = (X.shape[1], 32, 32, 3)
+    sizes = (X.shape[1], 32, 32, T.shape[1])
     params = [[rng.standard_normal((o, i)) * np.sqrt(2.0 / (i + o)), np.zeros(o)] for i, o in zip(sizes[:-1], sizes[1:])]
     m = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
     v = [[np.zeros_like(W), np.zeros_like(b)] for W, b in params]
