@@ -477,7 +477,7 @@ def run_ours(args, rank, world, local):
             pms, pcalls = at_.profile_read()
             at_.profile(False)
             res[name] = (tot / reps / 1e3 / iters, fl[-1] if fl else None,
-                         float(pms.sum()) / max(1, int(pcalls.min())))
+                         float(np.sum(pms)) / max(1, int(np.min(pcalls))))
             del U, W
         at32.close()
         at16.close()
