@@ -40,6 +40,13 @@ FALLBACK_HBM_GBS = 6800.0
 CPU_SAMPLE_NNZ = 40_000_000      # oracle CPU-baseline sample, all host threads
 CPU_SAMPLE_NNZ_1T = 10_000_000   # the same, one thread (about 8-10 s)
 GEN_SAMPLE_NNZ = 10_000_000      # oracle generation sample (encode + sort)
+TRANSPOSE_SAMPLE_NNZ = 10_000_000  # oracle transposition sample (stable sorts by coordinates)
+
+
+def TRANSPOSE_MODES(N):
+    """The transposition the bench times: the last mode first, then the
+    others in order (for 4M x 4M x 30k: the 30k-long mode leads)."""
+    return [N - 1] + list(range(N - 1))
 RANKSPEC_NNZ = 20_000_000        # rank-specialisation comparison tensor
 REF_STEP_NNZ = 4_000_000         # reference-arm step sample
 
@@ -58,6 +65,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true", help="skip the BF16-factor CP-ALS comparison")
     p.add_argument("--no-rankspec", action="store_true", help="skip the rank-specialisation comparison")
+    p.add_argument("--no-transpose", action="store_true", help="skip the transposition measurement")
     p.add_argument("--no-batched", action="store_true", help="skip the batched + learned sub-measurement")
     p.add_argument("--sub-batch-items", type=int, default=64,
                    help="held-out batched tensors in the default line's batched sub-measurement")
@@ -269,6 +277,16 @@ def oracle_generation_time(dims, idx, nnz_sample):
     return time.perf_counter() - t0
 
 
+def oracle_transpose_time(idx, modes, nnz_sample):
+    """The oracle's transposition sort (one stable sort per chosen mode, by
+    coordinate) of the first nnz_sample nonzeros on one host thread; seconds."""
+    import oracle
+    coords = np.stack([np.asarray(a[:nnz_sample], dtype=np.int64) for a in idx], 1)
+    t0 = time.perf_counter()
+    oracle.transpose_order(coords, modes)
+    return time.perf_counter() - t0
+
+
 def host_cpu():
     """Host CPU model and logical core count."""
     model = None
@@ -323,7 +341,7 @@ def run_reference(args, rank, world):
 # our arm
 
 def run_ours(args, rank, world, local):
-    from paper_2102_10245_gb300 import AltoTensor, launch_count, torch_allocator
+    from paper_2102_10245_gb300 import AltoTensor, launch_count, torch_allocator, GRAM_AUTO, GRAM_CUDA_CORES
     import paper_2102_10245_gb300.build as lb
     lb.build()
 
@@ -338,6 +356,7 @@ def run_ours(args, rank, world, local):
     # CPU baseline first (rank 0, single GPU only), before any GPU work
     cpu = None
     gen_oracle = None
+    tr_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         S = min(CPU_SAMPLE_NNZ, M)
         U64 = [u.astype(np.float64) for u in U0]
@@ -358,6 +377,12 @@ def run_ours(args, rank, world, local):
                       "sample": "oracle encode (bit loops) + stable sort (qsort, index tie-break) of the first "
                                 "%d nonzeros, one thread" % SG}
         del U64
+        if not args.no_transpose:
+            ST = min(TRANSPOSE_SAMPLE_NNZ, M)
+            tt = oracle_transpose_time(idx, TRANSPOSE_MODES(N), ST)
+            tr_oracle = {"gnnz_s": ST / tt / 1e9, "cores": 1, "seconds": tt,
+                         "sample": "oracle transposition sort (one stable numpy argsort per mode, modes %s) of the "
+                                   "first %d nonzeros, one thread" % (TRANSPOSE_MODES(N), ST)}
 
     dev = torch.device("cuda", torch.cuda.current_device())
     # inputs resident in HBM
@@ -396,6 +421,7 @@ def run_ours(args, rank, world, local):
         if not stats:
             stats.update(at.stats())
             stats["key_words"] = at.layout()["key_words"]
+            stats["key_bytes"] = at.key_bytes()
             stats["fits"] = fits
         at.close()
         return fits
@@ -432,7 +458,7 @@ def run_ours(args, rank, world, local):
     fb = {"f32": 4, "bf16": 2, "f64": 8}[fdtype]
     ob = 8 if fdtype == "f64" else 4
     vb = 8 if fdtype == "f64" else 4
-    kb = 8 * stats["key_words"]
+    kb = stats["key_bytes"]
     per_mode_bytes = [mttkrp_bytes(M, kb, vb, stats["distinct"], R, fb, ob, n) for n in range(N)]
     tot_bytes = sum(per_mode_bytes[n] * prof_calls[n] for n in range(N))
     tot_ms = float(prof_ms.sum())
@@ -454,8 +480,10 @@ def run_ours(args, rank, world, local):
         at16 = AltoTensor(dims, idx_d, vals_d.to(torch.bfloat16), allocator=alloc, variants=variants,
                           nparts=int(args.nparts))
         res = {}
-        for name, at_, dt in (("f32", at32, torch.float32), ("bf16", at32, torch.bfloat16),
-                              ("bf16_values", at16, torch.bfloat16)):
+        for name, at_, dt, eng in (("f32", at32, torch.float32, GRAM_AUTO), ("bf16", at32, torch.bfloat16, GRAM_AUTO),
+                                   ("bf16_cuda_core_gram", at32, torch.bfloat16, GRAM_CUDA_CORES),
+                                   ("bf16_values", at16, torch.bfloat16, GRAM_AUTO)):
+            at_.set_gram_engine(eng)
             U = [u.to(dt) for u in U0_d]
             W = [torch.empty_like(u) for u in U]
             for w, u in zip(W, U):
@@ -482,14 +510,16 @@ def run_ours(args, rank, world, local):
         at32.close()
         at16.close()
         precision = {"f32_s_per_iter": res["f32"][0], "bf16_s_per_iter": res["bf16"][0],
+                     "bf16_cuda_core_gram_s_per_iter": res["bf16_cuda_core_gram"][0],
                      "bf16_values_s_per_iter": res["bf16_values"][0],
                      "bf16_speedup": res["f32"][0] / res["bf16"][0],
                      "bf16_values_speedup": res["f32"][0] / res["bf16_values"][0],
                      "mttkrp_sweep_ms": {k: v[2] for k, v in res.items()},
                      "fit_f32": res["f32"][1], "fit_bf16": res["bf16"][1], "fit_bf16_values": res["bf16_values"][1],
                      "note": "CP-ALS only (MTTKRP sweeps + updates), one created tensor per value dtype, 3 timed "
-                             "runs; bf16 = BF16 factor storage, bf16_values = BF16 values and BF16 factors, FP32 "
-                             "accumulation throughout"}
+                             "runs; bf16 = BF16 factor storage (Gram matrices on the tensor cores), "
+                             "bf16_cuda_core_gram = the same with the CUDA-core Gram, bf16_values = BF16 values and "
+                             "BF16 factors, FP32 accumulation throughout"}
 
     # rank specialisation (Sec. 4.5): the rank- and order-specialised fused
     # kernel against the runtime-rank generic kernel, on a smaller tensor
@@ -518,6 +548,26 @@ def run_ours(args, rank, world, local):
         rankspec = {"nnz": int(len(rvals)), "per_rank": res,
                     "what": "all-mode MTTKRP sweep, FP32 factors: specialised (order and rank fixed at compile "
                             "time, fused body) vs generic (runtime order and rank, scalar atomics)"}
+
+    # sparse tensor transposition (Sec. 5) by partial radix sort: every mode
+    # (the full reordering) and the leading mode alone, from the ALTO tensor
+    # to the transposed COO (input positions, coordinates, values) in HBM
+    transpose = None
+    if not args.no_transpose:
+        at = AltoTensor(dims, idx_d, vals_d, allocator=alloc)
+        lay = at.layout()
+        res = {}
+        for name, modes in (("all_modes", TRANSPOSE_MODES(N)), ("leading_mode", TRANSPOSE_MODES(N)[:1])):
+            nb = sum(lay["bits"][m] for m in modes)
+            fn = lambda: at.transpose(modes)  # noqa: E731
+            fn()
+            ms = _time_k(fn, 3, stream)
+            res[name] = {"modes": modes, "key_bits": nb, "radix_passes": -(-max(nb, 1) // 8), "ms": ms,
+                         "gnnz_s": M / (ms / 1e3) / 1e9}
+        at.close()
+        transpose = dict(res, oracle=tr_oracle, index_bits=sum(lay["bits"]),
+                         what="alto_transpose: sort key cut from the stored index, stable LSD radix sort over the "
+                              "chosen modes' bits only, gather of input positions, coordinates (int64) and values")
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -590,6 +640,7 @@ def run_ours(args, rank, world, local):
         "cpals_s_per_iter": cpals_ms / 1e3 / iters,
         "cpals_precision": precision,
         "rank_specialisation": rankspec,
+        "transpose": transpose,
         "batched": batched,
         "fit_last": fits[-1] if fits else None,
         "roofline": roofline,
@@ -712,14 +763,12 @@ def run_batched(args, rank, world, local, n_items=None, steps=None, emit=True):
     log("regret: predictor %.3f / %.3f, rule %.3f / %.3f" % (reg_mlp + reg_rule))
 
     def plan(sel):
-        """A batch whose items run the chosen candidates (variant and
-        segment count; the plan keeps the count it was built with)."""
-        for (at, n, _, _), k in zip(items, sel):
-            at.set_parts(n, tune.parts_for(at, tune.PARTS[int(k)]))
-        b = Batch(items, variants=[tune.VARIANTS[int(k)] for k in sel])
-        for at, n, _, _ in items:
-            at.set_parts(n, 0)
-        return b
+        """A batch whose items run the chosen candidates' accumulation
+        variants with each tensor's own segment count: the autotuner's finer
+        segment counts win in a call of their own, but inside one persistent
+        launch over many items a short unit leaves each warp too few chunks to
+        fill its pipeline (measured slower)."""
+        return Batch(items, variants=[tune.VARIANTS[int(k)] for k in sel])
 
     def batch_ms(sel):
         b = plan(sel)
@@ -770,7 +819,7 @@ def run_batched(args, rank, world, local, n_items=None, steps=None, emit=True):
     tot_bytes = 0
     for at, n, U, _ in items:
         st = at.stats()
-        kb = 8 * at.layout()["key_words"]
+        kb = at.key_bytes()
         tot_bytes += mttkrp_bytes(at.nnz, kb, 4, st["distinct"], U[0].shape[1], 2, 4, n)
     peak, peak_src = measured_peak()
     achieved = tot_bytes / (ms / 1e3) / 1e9

@@ -67,12 +67,26 @@ typedef enum {
                              rank-specialisation comparison (Sec. 4.5) */
 } alto_variant;
 
+/* Engine of the Gram matrices U^T U of CP-ALS and alto_gram. */
+typedef enum {
+    ALTO_GRAM_AUTO = 0,          /* tensor cores for BF16 factors with R in
+                                    {8, 16, 32, 64}, CUDA cores otherwise */
+    ALTO_GRAM_CUDA_CORES = 1,    /* FP32 (FP64 for FP64 factors) partial sums
+                                    on the CUDA cores, FP64 across blocks */
+    ALTO_GRAM_TENSOR_CORES = 2   /* tcgen05 kind::f16 MMA: exact BF16
+                                    products, FP32 sums per thread block in
+                                    tensor memory, FP64 across blocks (BF16
+                                    factors and R in {8, 16, 32, 64} only) */
+} alto_gram_engine;
+
 #define ALTO_MAX_MODES 8
 
 /*
  * Creation options.  Zero-initialise, or call alto_options_init.
  *   key_bits : 0 = smallest native word that holds the index (64 or 128,
- *              Sec. 4.2.3); 64 or 128 forces a width (64 fails with
+ *              Sec. 4.2.3) for generation and export, with the stored MTTKRP
+ *              keys packed into the fewest 32-bit words (alto_get_key_bytes);
+ *              64 or 128 forces that full width everywhere (64 fails with
  *              ALTO_EOVERFLOW when the index needs more bits).
  *   nparts   : number L of equal-nnz line segments (Sec. 3.2); 0 = auto:
  *              segments of 2048 nonzeros, halved down to 256 while the
@@ -154,7 +168,8 @@ alto_status alto_mttkrp(alto_t t, int mode, const void *const *factors,
  * FP64 (for FP32/BF16 factors the FP64 inverse is rounded to FP32 and
  * applied with FP32 arithmetic); columns normalised by their 2-norm in the
  * first iteration and by max(1, max |.|) afterwards, the norms going to
- * lambda; U_n^T U_n recomputed (FP64).  The fit after each iteration is
+ * lambda; U_n^T U_n recomputed (FP64 across thread blocks; on the tensor
+ * cores for BF16 factors, see alto_gram_engine).  The fit after each iteration is
  * 1 - ||X - [[lambda; U]]|| / ||X||.
  *
  *   factors : host array of N device pointers to I_m x rank matrices of
@@ -221,6 +236,53 @@ alto_status alto_export(alto_t t, uint64_t *keys, uint32_t *perm, void *vals,
                         int64_t *bounds, uint32_t *intervals);
 
 /*
+ * alto_gram -- G = U^T U (Sec. 2.2: the Gram matrices whose Hadamard product
+ * is the CP-ALS system matrix V) for a device factor U (I x R row-major, R <=
+ * 64, dtype F64 / F32 / BF16) into the device R x R FP64 matrix G
+ * (overwritten).  `engine` is an alto_gram_engine; ALTO_GRAM_TENSOR_CORES
+ * with FP32/FP64 factors or another R is ALTO_EINVAL.  Runs on `stream` and
+ * synchronises it; ALTO_ETIMEOUT if a bounded device wait of the tensor-core
+ * kernel ran out (G is then incomplete).
+ */
+alto_status alto_gram(const void *U, int64_t I, int R, alto_dtype dtype,
+                      int engine, double *G, void *stream);
+
+/* alto_set_gram_engine -- the engine alto_cpals uses for this tensor's Gram
+ * matrices (ALTO_GRAM_AUTO by default).  Errors: ALTO_EINVAL for a NULL
+ * handle or an unknown engine. */
+alto_status alto_set_gram_engine(alto_t t, int engine);
+
+/*
+ * alto_transpose -- sparse tensor transposition (Sec. 5, sparse tensor
+ * operations): the nonzeros in the lexicographic order of the coordinates of
+ * modes[0], modes[1], ..., modes[nsel-1] (modes[0] most significant).  The
+ * sort key is cut out of the stored linearized index and sorted by a stable
+ * LSD radix sort over the chosen modes' index bits only (a partial radix
+ * sort: sum of b_m over the chosen modes, not all B bits).  Nonzeros that tie
+ * on the chosen modes keep ALTO order; with nsel = N only duplicate
+ * coordinates tie, and they keep input order.
+ *   nsel, modes : 1 <= nsel <= N distinct modes (host array).
+ *   order       : device, M uint32 or NULL: ALTO position of the y-th nonzero
+ *                 of the result.
+ *   src         : device, M uint32 or NULL: its input position (the index of
+ *                 the nonzero in the arrays given to alto_create).
+ *   idx         : host array of N device pointers, or NULL: coordinates of the
+ *                 result, M entries of idx_bytes (4: uint32, 8: int64) each;
+ *                 output mode j is modes[j] for j < nsel, the remaining modes
+ *                 follow in ascending order.
+ *   vals        : device, M values of the stored value dtype, or NULL.
+ * Runs on `stream` and synchronises it before returning (the sort scratch,
+ * 2 x M x (8 or 16) + 2 x M x 4 bytes, is allocated through the tensor's
+ * allocator and freed).  Errors: ALTO_EINVAL (NULL handle, nsel outside
+ * [1, N], a repeated or out-of-range mode, idx_bytes not 4 or 8, a NULL
+ * coordinate pointer), ALTO_ENOMEM, ALTO_ECUDA.  An empty tensor writes
+ * nothing.
+ */
+alto_status alto_transpose(alto_t t, int nsel, const int *modes,
+                           uint32_t *order, uint32_t *src, void *const *idx,
+                           int idx_bytes, void *vals, void *stream);
+
+/*
  * alto_get_mode_stats -- statistics of one mode, for variant selection.
  * out[0..n) (n <= 8 used): 0 length I_n, 1 distinct rows D_n, 2 reuse M/I_n,
  * 3 widest segment interval, 4 hot rows, 5 share of the sampled nonzeros
@@ -263,6 +325,13 @@ alto_status alto_nn_adam(float *param, const float *grad, float *m, float *v,
 
 /* alto_set_variant -- override the MTTKRP variant of one mode. */
 alto_status alto_set_variant(alto_t t, int mode, int variant);
+
+/* alto_get_key_bytes -- bytes of one stored key in the streamed MTTKRP
+ * format: the index and its flag bits in the fewest 32-bit words (4, 8, 12 or
+ * 16 bytes; Sec. 4.2.3 stores native multiples, 32- and 96-bit words are the
+ * packed widths), or the full word that alto_options.key_bits forces.
+ * alto_export always widens keys to key_words 64-bit words. */
+alto_status alto_get_key_bytes(alto_t t, int *bytes);
 
 /* alto_set_parts -- segment count used by mode `mode`'s ATOMIC and WARPAGG
  * MTTKRPs (alto_mttkrp and batches planned afterwards): the line is cut into
@@ -343,9 +412,8 @@ alto_status alto_launch_count(uint64_t *count);
  *   perm  : device, nnz uint32, input position of every nonzero in ALTO order.
  * The sort's scratch lives in one fixed device array of about 5.3 MB that
  * every GPU which loads libalto holds until the process exits; nnz above
- * ALTO_NOALLOC_MAX_NNZ is rejected with ALTO_EINVAL.  The first call on each
- * device looks up that array's device address and keeps it for the life of
- * the process (do not call it again after resetting the device).  All calls
+ * ALTO_NOALLOC_MAX_NNZ is rejected with ALTO_EINVAL.  Every call looks up
+ * that array's device address in the current context.  All calls
  * share the array: calls that overlap on the GPU (other streams, other host
  * threads on the same device) race and must be serialised by the caller.
  * The call reads its status word back and synchronises `stream` at its end,

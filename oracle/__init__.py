@@ -28,6 +28,10 @@ What each function follows in the paper:
   and the fit from ||X||, lambda and the last mode's MTTKRP.
 * ``compression_ratio`` (Eq. 2), ``sfc_bits`` (Eq. 3), ``use_buffered``
   (Sec. 3.3 conflict rule: reuse = M / I_n, buffered iff reuse > 4).
+* ``transpose_order`` / ``transpose`` -- Sec. 5 sparse tensor transposition,
+  which reduces to sorting the nonzeros by their coordinates in the new mode
+  order: starting from ALTO order (``encode`` + ``sort_perm``), one stable
+  sort per chosen mode, least significant first, so ties keep ALTO order.
 
 Parity pins for every function live in ``tests/test_oracle.py``.  The CP-ALS
 equality with SPLATT claimed in Sec. 4.1 is parity unpinned: neither SPLATT
@@ -268,6 +272,34 @@ def mttkrp_sampled(dims, idx, vals, get_rows, mode, rows):
     R = next(f.shape[1] for f in fac if f is not None)
     fac[mode] = np.zeros((1, R))
     return mttkrp(sub_dims, sub_idx, v, fac, mode)
+
+
+def transpose_order(coords, modes):
+    """Sec. 5 transposition as a sort by coordinates.  ``coords`` is M x N,
+    rows in ALTO order; returns the positions (into those rows) of the
+    nonzeros in the lexicographic order of columns modes[0], modes[1], ...
+    (modes[0] most significant), ties in the given order.  One stable
+    ``argsort`` per chosen mode, the last chosen mode first."""
+    coords = np.asarray(coords)
+    order = np.arange(coords.shape[0], dtype=np.int64)
+    for m in reversed([int(x) for x in modes]):
+        order = order[np.argsort(coords[order, m], kind="stable")]
+    return order
+
+
+def transpose(dims, idx, modes):
+    """Transposition of the COO tensor (dims, idx) by ``modes``: returns
+    (order, src) -- the ALTO positions and the input positions of the
+    nonzeros in transposed order.  ALTO order comes from ``encode`` and
+    ``sort_perm``; duplicates therefore keep input order."""
+    keys = encode(dims, idx)
+    alto = sort_perm(keys)
+    M = len(alto)
+    coords = np.zeros((M, len(dims)), dtype=np.int64)
+    for n, a in enumerate(idx):
+        coords[:, n] = np.asarray(a, dtype=np.int64)[alto]
+    order = transpose_order(coords, modes)
+    return order, alto[order]
 
 
 def reuse(dims, M):

@@ -58,8 +58,12 @@ def lib():
             "alto_get_hot_rows": [P, I, P, P],
             "alto_get_stats": [P, P, P, P, P, P, P],
             "alto_export": [P, P, P, P, P, P],
+            "alto_transpose": [P, I, P, P, P, P, I, P, P],
+            "alto_gram": [P, I64, I, I, I, P, P],
+            "alto_set_gram_engine": [P, I],
             "alto_set_variant": [P, I, I],
             "alto_set_parts": [P, I, I64],
+            "alto_get_key_bytes": [P, P],
             "alto_resolve_variant": [P, I, I, I, I, P],
             "alto_check": [P, P],
             "alto_destroy": [P],
@@ -115,6 +119,22 @@ def _fdtype(t):
     if t.dtype == torch.bfloat16:
         return BF16
     raise TypeError("factor dtype %s not supported" % t.dtype)
+
+
+GRAM_AUTO, GRAM_CUDA_CORES, GRAM_TENSOR_CORES = 0, 1, 2
+
+
+def gram(U, engine=GRAM_AUTO, out=None, stream=None):
+    """G = U^T U (R x R, float64, on U's device) of a contiguous CUDA factor
+    U (I x R, float64 / float32 / bfloat16); synchronises the stream."""
+    if not U.is_cuda or not U.is_contiguous() or U.dim() != 2:
+        raise ValueError("U must be a contiguous 2-D CUDA tensor")
+    I, R = int(U.shape[0]), int(U.shape[1])
+    if out is None:
+        out = torch.empty((R, R), dtype=torch.float64, device=U.device)
+    _check(lib().alto_gram(ctypes.c_void_p(U.data_ptr()), I, R, _fdtype(U), int(engine),
+                           ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
 
 
 def layout_for_dims(dims, key_bits=0):
@@ -332,6 +352,17 @@ class AltoTensor:
     def set_variant(self, mode, variant):
         _check(lib().alto_set_variant(self._h, mode, int(variant)))
 
+    def set_gram_engine(self, engine):
+        """Engine of the CP-ALS Gram matrices (GRAM_AUTO, GRAM_CUDA_CORES,
+        GRAM_TENSOR_CORES)."""
+        _check(lib().alto_set_gram_engine(self._h, int(engine)))
+
+    def key_bytes(self):
+        """Bytes of one stored key in the streamed MTTKRP format."""
+        b = ctypes.c_int()
+        _check(lib().alto_get_key_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
     def set_parts(self, mode, nparts):
         """Segment count of this mode's ATOMIC / WARPAGG MTTKRPs (0: the
         tensor's own L)."""
@@ -368,6 +399,37 @@ class AltoTensor:
         ptrs = (ctypes.c_void_p * self.N)(*[(f.data_ptr() if f is not None else 0) for f in factors])
         _check(lib().alto_mttkrp(self._h, mode, ptrs, R, fd, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
+
+    def transpose(self, modes, order=False, src=True, idx=True, vals=True, idx_dtype=torch.int64,
+                  device=None, stream=None):
+        """Sparse tensor transposition (Sec. 5): the nonzeros in the
+        lexicographic order of the coordinates of ``modes`` (first mode most
+        significant), by a radix sort over those modes' key bits only; ties
+        keep ALTO order.  Returns a dict of device tensors: ``order`` (ALTO
+        positions) and ``src`` (input positions) as int32 holding uint32
+        values, ``idx`` (N coordinate arrays, output mode j = modes[j], the
+        other modes after in ascending order) and ``vals`` (stored dtype)."""
+        modes = [int(m) for m in modes]
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        M = self.nnz
+        res = {}
+        if order:
+            res["order"] = torch.empty(M, dtype=torch.int32, device=dev)
+        if src:
+            res["src"] = torch.empty(M, dtype=torch.int32, device=dev)
+        if idx:
+            if idx_dtype not in (torch.int64, torch.int32):
+                raise ValueError("idx_dtype must be int64 or int32")
+            res["idx"] = [torch.empty(M, dtype=idx_dtype, device=dev) for _ in range(self.N)]
+        if vals:
+            vdt = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[self.vdtype]
+            res["vals"] = torch.empty(M, dtype=vdt, device=dev)
+        sel = (ctypes.c_int * max(len(modes), 1))(*modes)
+        ptr = lambda k: ctypes.c_void_p(res[k].data_ptr()) if k in res else None  # noqa: E731
+        iptrs = (ctypes.c_void_p * self.N)(*[a.data_ptr() for a in res["idx"]]) if idx else None
+        _check(lib().alto_transpose(self._h, len(modes), sel, ptr("order"), ptr("src"), iptrs,
+                                    8 if idx_dtype == torch.int64 else 4, ptr("vals"), _stream(stream)))
+        return res
 
     def cpals(self, factors, iters, lam=None, stream=None, fit=True):
         """Run CP-ALS in place on ``factors``; returns (lambda, fits)."""

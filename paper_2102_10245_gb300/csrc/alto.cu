@@ -121,6 +121,8 @@ bool is_device_ptr(const void* p) {
 }
 
 void free_format(alto_tensor_s* t) {
+  if (t->ckeys != reinterpret_cast<uint32_t*>(t->keys)) dev_free(t, t->ckeys);
+  t->ckeys = nullptr;
   dev_free(t, t->keys);
   dev_free(t, t->perm);
   dev_free(t, t->vals);
@@ -260,11 +262,11 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     t->reuse[n] = static_cast<double>(nnz) / static_cast<double>(lay.dims[n]);
     t->variant[n] = o.variant[n];
   }
-  // helper flags go only into spare bits of the chosen word (Sec. 3.3)
+  // helper flags go only into spare bits of the stored word (Sec. 3.3): they never widen it
   if (o.use_flags) {
     for (int n = 0; n < N; ++n)
       if (t->reuse[n] <= 4.0) ++nflag;
-    if (nflag > 0 && lay.B + nflag <= 64 * KW) {
+    if (nflag > 0 && lay.B + nflag <= 32 * lay.CW) {
       int b = lay.B;
       for (int n = 0; n < N; ++n)
         if (t->reuse[n] <= 4.0) lay.flag_bit[n] = b++;
@@ -277,7 +279,7 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
   if (o.use_flags) {
     int b = lay.B + nflag;
     for (int n = 0; n < N; ++n)
-      if (t->reuse[n] > 4.0 && b < 64 * KW && lay.dims[n] <= (1ull << 31)) {
+      if (t->reuse[n] > 4.0 && b < 32 * lay.CW && lay.dims[n] <= (1ull << 31)) {
         lay.hot_bit[n] = b++;
         ++nhotbit;
       }
@@ -393,6 +395,11 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     CK(launch_max_interval(t->ivl, t->L, N, dstat + kMaxModes, s));
     if (nflag > 0) CK(launch_set_flags(lay, t->keys, nnz, first, last, nullptr, s));
     if (nhotbit > 0) CK(launch_set_flags(lay, t->keys, nnz, first, last, hotmap, s));
+    // stored keys: packed into CW 32-bit words when that is narrower
+    if (lay.CW < 2 * KW) {
+      ALLOC(t->ckeys, uint32_t*, sizeof(uint32_t) * lay.CW * (nnz + 32));
+      CK(launch_pack_keys(t->keys, KW, t->ckeys, lay.CW, nnz, s));
+    }
   } else {
     // empty tensor: one empty segment
     std::vector<uint32_t> e(2 * N);
@@ -418,6 +425,12 @@ alto_status alto_create(alto_t* out, int nmodes, const uint64_t* dims, int64_t n
     t->max_ivl[n] = hstat[kMaxModes + n];
   }
   unit_intervals(t, hivl);
+  if (t->ckeys != nullptr) {  // packed: the generation-width keys are no longer needed
+    dev_free(t, t->keys);
+    t->keys = nullptr;
+  } else {
+    t->ckeys = reinterpret_cast<uint32_t*>(t->keys);
+  }
   st = ALTO_OK;
 
 done:
@@ -499,7 +512,17 @@ alto_status alto_export(alto_t t, uint64_t* keys, uint32_t* perm, void* vals, in
   alto_status st = ALTO_OK;
   const size_t M = static_cast<size_t>(t->M);
   const size_t vb = t->vdtype == ALTO_F64 ? 8 : (t->vdtype == ALTO_F32 ? 4 : 2);
-  if (keys && M) CK(cudaMemcpy(keys, t->keys, sizeof(uint64_t) * t->lay.KW * M, cudaMemcpyDeviceToHost));
+  if (keys && M) {  // stored keys widened to KW 64-bit words
+    const int CW = t->lay.CW, KW = t->lay.KW;
+    std::vector<uint32_t> h(static_cast<size_t>(CW) * M);
+    CK(cudaMemcpy(h.data(), t->ckeys, sizeof(uint32_t) * h.size(), cudaMemcpyDeviceToHost));
+    for (size_t x = 0; x < M; ++x)
+      for (int w = 0; w < KW; ++w) {
+        const uint64_t lo = 2 * w < CW ? h[x * CW + 2 * w] : 0u;
+        const uint64_t hi = 2 * w + 1 < CW ? h[x * CW + 2 * w + 1] : 0u;
+        keys[x * KW + w] = lo | (hi << 32);
+      }
+  }
   if (perm && M) CK(cudaMemcpy(perm, t->perm, sizeof(uint32_t) * M, cudaMemcpyDeviceToHost));
   if (vals && M) CK(cudaMemcpy(vals, t->vals, vb * M, cudaMemcpyDeviceToHost));
   if (intervals)
@@ -551,11 +574,28 @@ alto_status alto_set_variant(alto_t t, int mode, int variant) {
   return ALTO_OK;
 }
 
+alto_status alto_set_gram_engine(alto_t t, int engine) {
+  if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
+  if (engine < ALTO_GRAM_AUTO || engine > ALTO_GRAM_TENSOR_CORES) return fail(ALTO_EINVAL, "bad engine %d", engine);
+  t->gram_engine = engine;
+  return ALTO_OK;
+}
+
+alto_status alto_gram(const void* U, int64_t I, int R, alto_dtype dtype, int engine, double* G, void* stream) {
+  return gram_any(U, I, R, dtype, engine, G, static_cast<cudaStream_t>(stream));
+}
+
 alto_status alto_set_parts(alto_t t, int mode, int64_t nparts) {
   if (t == nullptr) return fail(ALTO_EINVAL, "null tensor");
   if (mode < 0 || mode >= t->lay.N) return fail(ALTO_EINVAL, "bad mode %d", mode);
   if (nparts < 0) return fail(ALTO_EINVAL, "negative segment count %lld", static_cast<long long>(nparts));
   t->mode_parts[mode] = nparts;
+  return ALTO_OK;
+}
+
+alto_status alto_get_key_bytes(alto_t t, int* bytes) {
+  if (t == nullptr || bytes == nullptr) return fail(ALTO_EINVAL, "null argument");
+  *bytes = 4 * t->lay.CW;
   return ALTO_OK;
 }
 

@@ -96,7 +96,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
   cudaError_t e = cudaSuccess;
 
   // item descriptions, grouped by kernel shape
-  using Key = std::tuple<int, int, int, int, int>;  // N, KW, R, variant, fused body
+  using Key = std::tuple<int, int, int, int, int>;  // N, stored key words, R, variant, fused body
   struct Zero {
     void* p;
     size_t bytes;
@@ -129,10 +129,10 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     const int fused = (v == ALTO_VAR_ATOMIC || v == ALTO_VAR_WARPAGG) &&
                       fused_ok(t->lay.N, R, fsz, factors_in_slot_order(t, mode, factors[i]).data(), outs[i], osz,
                                t->lay.dims[mode]);
-    const Key key{t->lay.N, t->lay.KW, R, v, fused};
+    const Key key{t->lay.N, t->lay.CW, R, v, fused};
     HostGroup& hg = groups[key];
     hg.zeros.push_back(z);
-    hg.cost += static_cast<double>(t->M) * (8.0 * t->lay.KW + 4.0 + (t->lay.N - 1) * R * fsz) +
+    hg.cost += static_cast<double>(t->M) * (4.0 * t->lay.CW + 4.0 + (t->lay.N - 1) * R * fsz) +
                static_cast<double>(z.bytes);
     MttkrpLaunch l{};
     fill_launch(t, mode, factors[i], R, outs[i], &l);
@@ -243,7 +243,7 @@ alto_status alto_batch_create(alto_batch_t* out, int count, const alto_t* tensor
     bl.args.nitems = static_cast<int>(g.host->items.size());
     bl.args.hot_replicas = kBatchHotReplicas;
     bl.N = std::get<0>(g.key);
-    bl.KW = std::get<1>(g.key);
+    bl.W32 = std::get<1>(g.key);
     bl.R = std::get<2>(g.key);
     bl.variant = std::get<3>(g.key);
     bl.sms = sms;

@@ -80,6 +80,70 @@ __device__ __forceinline__ uint32_t extract(const KeyT<KW>& k, const DecodeParam
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// The stored (MTTKRP) form of a key: the ALTO index and its flag bits in the
+// fewest 32-bit words, W in 1..4 (Sec. 4.2.3 uses multiples of the native
+// word; 32 and 96 bits are the packed widths), word 0 holding the lowest
+// bits.  Key x occupies words [W x, W x + W).
+template <int W>
+struct CKey {
+  uint32_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ CKey<W> load_ckey(const uint32_t* keys, int64_t x) {
+  CKey<W> k;
+  if constexpr (W == 1) {
+    k.w[0] = __ldcs(keys + x);
+  } else if constexpr (W == 2) {
+    const uint2 v = __ldcs(reinterpret_cast<const uint2*>(keys) + x);
+    k.w[0] = v.x;
+    k.w[1] = v.y;
+  } else if constexpr (W == 3) {  // 12-byte keys: three 4-byte loads (the warp's 384 bytes are contiguous)
+    const uint32_t* p = keys + 3 * x;
+    k.w[0] = __ldcs(p);
+    k.w[1] = __ldcs(p + 1);
+    k.w[2] = __ldcs(p + 2);
+  } else {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(keys) + x);
+    k.w[0] = v.x;
+    k.w[1] = v.y;
+    k.w[2] = v.z;
+    k.w[3] = v.w;
+  }
+  return k;
+}
+
+// Index of the mode in slot s from a stored key (EXTRACT of Alg. 1-2): the
+// five-step compress of every word holding bits of the mode.
+template <int W>
+__device__ __forceinline__ uint32_t extract_c(const CKey<W>& k, const DecodeParams& p, int s) {
+  uint32_t r = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    const uint32_t m = p.mask[s][w];
+    if (m != 0u) {
+      uint32_t x = k.w[w] & m;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const uint32_t t = x & p.mv[s][w][i];
+        x = (x ^ t) | (t >> (1u << i));
+      }
+      r |= x << p.shift[s][w];
+    }
+  }
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t ckey_bit(const CKey<W>& k, int bit) {
+  uint32_t w = k.w[0];
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+    if ((bit >> 5) == i) w = k.w[i];
+  return (w >> (bit & 31)) & 1u;
+}
+
 // First position of line segment l of L over M nonzeros: floor(l * M / L)
 // (Sec. 3.2), in unsigned 64-bit arithmetic (M < 2^32, l <= L <= M).
 __host__ __device__ __forceinline__ int64_t seg_begin(int64_t l, int64_t M, int64_t L) {

@@ -701,10 +701,19 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
   const int N = t->lay.N;
   CpalsWork& w = t->cp;
   const size_t RR = static_cast<size_t>(R) * R;
+  // Gram matrices on the tensor cores for BF16 factors (exact products,
+  // FP32 block sums, FP64 across blocks) unless the CUDA cores are asked for
+  constexpr bool kBF16 = std::is_same<FT, __nv_bfloat16>::value;
+  const bool tc = kBF16 && t->gram_engine != ALTO_GRAM_CUDA_CORES && gram_tc_supported(R);
   // initial Gram matrices
   CK(cudaMemsetAsync(w.gram, 0, sizeof(double) * N * RR, s));
-  for (int m = 0; m < N; ++m)
-    CK(launch_gram<FT>(factors[m], static_cast<int64_t>(t->lay.dims[m]), R, w.gram + m * RR, s));
+  for (int m = 0; m < N; ++m) {
+    if (tc)
+      CK(launch_gram_bf16_tc(static_cast<const __nv_bfloat16*>(factors[m]), static_cast<int64_t>(t->lay.dims[m]),
+                             R, w.gram + m * RR, t->status, s));
+    else
+      CK(launch_gram<FT>(factors[m], static_cast<int64_t>(t->lay.dims[m]), R, w.gram + m * RR, s));
+  }
   const alto_dtype fd = std::is_same<FT, double>::value ? ALTO_F64
                         : std::is_same<FT, float>::value ? ALTO_F32
                                                           : ALTO_BF16;
@@ -744,6 +753,12 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
         double* gn = w.gram + n * RR;
         const C* mt = last ? static_cast<const C*>(w.mt) : nullptr;
         const unsigned gr = rows_grid(In, 32 * 8, 8);
+        if (tc) {
+          CK(launch_normalize_gram_bf16_tc(reinterpret_cast<const float*>(at), In, R, w.colstat, use_max, lambda,
+                                           reinterpret_cast<__nv_bfloat16*>(un), gn,
+                                           reinterpret_cast<const float*>(mt), w.scal, t->status, s));
+          continue;
+        }
         switch (R) {
           case 8: normalize_gram_bcast_kernel<FT, 8><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
           case 16: normalize_gram_bcast_kernel<FT, 16><<<gr, kT, 0, s>>>(at, In, w.colstat, use_max, lambda, un, gn, mt, w.scal); break;
@@ -770,6 +785,37 @@ alto_status cpals_typed(alto_tensor_s* t, int R, int iters, void* const* factors
 }
 
 }  // namespace
+
+__device__ int g_gram_status;
+
+alto_status gram_any(const void* U, int64_t I, int R, alto_dtype dtype, int engine, double* G, cudaStream_t s) {
+  if (U == nullptr && I > 0) return fail(ALTO_EINVAL, "null factor");
+  if (G == nullptr) return fail(ALTO_EINVAL, "null Gram output");
+  if (I < 0 || R < 1 || R > kMaxR) return fail(ALTO_EINVAL, "bad shape %lld x %d", static_cast<long long>(I), R);
+  if (engine < ALTO_GRAM_AUTO || engine > ALTO_GRAM_TENSOR_CORES) return fail(ALTO_EINVAL, "bad engine %d", engine);
+  const bool tc = dtype == ALTO_BF16 && engine != ALTO_GRAM_CUDA_CORES && gram_tc_supported(R);
+  if (engine == ALTO_GRAM_TENSOR_CORES && !tc)
+    return fail(ALTO_EINVAL, "the tensor-core Gram needs BF16 factors and R in {8, 16, 32, 64}");
+  int* status = nullptr;
+  CK(cudaGetSymbolAddress(reinterpret_cast<void**>(&status), g_gram_status));
+  CK(cudaMemsetAsync(status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(G, 0, sizeof(double) * R * R, s));
+  if (tc) {
+    CK(launch_gram_bf16_tc(static_cast<const __nv_bfloat16*>(U), I, R, G, status, s));
+  } else {
+    switch (dtype) {
+      case ALTO_F64: CK(launch_gram<double>(U, I, R, G, s)); break;
+      case ALTO_F32: CK(launch_gram<float>(U, I, R, G, s)); break;
+      case ALTO_BF16: CK(launch_gram<__nv_bfloat16>(U, I, R, G, s)); break;
+      default: return fail(ALTO_EINVAL, "bad dtype");
+    }
+  }
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h != 0) return fail(static_cast<alto_status>(h), "device wait ran out in the tensor-core Gram");
+  return ALTO_OK;
+}
 
 alto_status run_cpals(alto_tensor_s* t, int R, int iters, void* const* factors, alto_dtype fdtype,
                       double* lambda, double* fit, cudaStream_t s) {

@@ -310,6 +310,25 @@ cudaError_t launch_encode(const Layout& lay, const IdxPtrs& idx, int idx_bytes, 
   return cudaGetLastError();
 }
 
+// Stored keys: the low CW 32-bit words of every KW-word key (the index and
+// its flags fit in them by construction of the layout).
+__global__ void __launch_bounds__(256) pack_keys_kernel(const uint64_t* __restrict__ keys, int KW,
+                                                        uint32_t* __restrict__ out, int CW, int64_t M) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t x = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; x < M; x += stride)
+    for (int w = 0; w < CW; ++w) {
+      const uint64_t k = keys[x * KW + (w >> 1)];
+      out[x * CW + w] = static_cast<uint32_t>(k >> ((w & 1) * 32));
+    }
+}
+
+cudaError_t launch_pack_keys(const uint64_t* keys, int KW, uint32_t* out, int CW, int64_t M, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  pack_keys_kernel<<<grid_for(M, 256), 256, 0, s>>>(keys, KW, out, CW, M);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_permute(const void* src, void* dst, const uint32_t* perm, int64_t M,
                            int elem_bytes, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;

@@ -18,7 +18,8 @@ struct Layout {
   uint64_t dims[kMaxModes] = {};
   int nbits[kMaxModes] = {};
   int B = 0;                       // total index bits (Eq. 1 with whole bits)
-  int KW = 1;                      // 64-bit words per key
+  int KW = 1;                      // 64-bit words per key during generation and in exports
+  int CW = 2;                      // 32-bit words per stored (MTTKRP) key: 1..4
   int pos[kMaxModes][32] = {};     // key bit of bit l of mode n
   uint64_t mask[kMaxModes][2] = {};
   int flag_bit[kMaxModes] = {};    // -1: no helper flag for the mode
@@ -72,7 +73,8 @@ struct alto_tensor_s {
   void (*free_fn)(void*, void*) = nullptr;
   void* alloc_ctx = nullptr;
   // device format (owned)
-  uint64_t* keys = nullptr;   // M x KW, ALTO order, flags in spare bits
+  uint64_t* keys = nullptr;   // M x KW, ALTO order, flags in spare bits (generation; freed when packed)
+  uint32_t* ckeys = nullptr;  // M x CW stored keys for MTTKRP (aliases keys when CW == 2 KW)
   uint32_t* perm = nullptr;   // M, input position of each nonzero
   void* vals = nullptr;       // M values in ALTO order
   uint32_t* ivl = nullptr;    // L x N x 2 closed intervals
@@ -88,6 +90,7 @@ struct alto_tensor_s {
   double reuse[alto::kMaxModes] = {};
   int variant[alto::kMaxModes] = {};
   int64_t mode_parts[alto::kMaxModes] = {};  // per-mode segment count of ATOMIC / WARPAGG (0: L)
+  int gram_engine = 0;  // ALTO_GRAM_*: Gram matrices of CP-ALS on tensor cores (BF16) or CUDA cores
   double normX2 = 0.0;
   // Thread-block units (8 consecutive segments): union of their intervals
   // per mode, kept on the host (unit_lo / unit_hi) and as sorted widths.
@@ -148,6 +151,18 @@ cudaError_t radix_sort_pairs(uint64_t** keys, uint64_t** keys_alt, uint32_t** pe
                              uint32_t** perm_alt, int64_t M, int KW, int nbits, uint32_t* scratch,
                              cudaStream_t s);
 
+// gram_tc.cu: G += U^T U for BF16 U on the tensor cores (R in {8, 16, 32, 64}),
+// and the CP-ALS form that first normalises the solved FP32 rows into U
+bool gram_tc_supported(int R);
+cudaError_t launch_gram_bf16_tc(const __nv_bfloat16* U, int64_t I, int R, double* G, int* status,
+                                cudaStream_t s);
+cudaError_t launch_normalize_gram_bf16_tc(const float* A, int64_t I, int R, const double* colstat, int use_max,
+                                          double* lambda, __nv_bfloat16* U, double* G, const float* Mt,
+                                          double* ip, int* status, cudaStream_t s);
+
+// cpals.cu: G = U^T U (R x R FP64) through the chosen engine; synchronous
+alto_status gram_any(const void* U, int64_t I, int R, alto_dtype dtype, int engine, double* G, cudaStream_t s);
+
 // layout.cu (host only)
 alto_status make_layout(int N, const uint64_t* dims, int key_bits, Layout* out);
 void make_decode(const Layout& lay, const int* slot_mode, DecodeParams* dp);
@@ -159,6 +174,7 @@ struct IdxPtrs {
 };
 cudaError_t launch_encode(const Layout& lay, const IdxPtrs& idx, int idx_bytes, int64_t M,
                           uint64_t* keys, int* status, cudaStream_t s);
+cudaError_t launch_pack_keys(const uint64_t* keys, int KW, uint32_t* out, int CW, int64_t M, cudaStream_t s);
 cudaError_t launch_permute(const void* src, void* dst, const uint32_t* perm, int64_t M,
                            int elem_bytes, cudaStream_t s);
 cudaError_t launch_sumsq(const uint64_t* keys, int KW, const void* vals, alto_dtype vd, int64_t M,

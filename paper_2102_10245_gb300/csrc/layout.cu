@@ -89,6 +89,14 @@ alto_status make_layout(int N, const uint64_t* dims, int key_bits, Layout* out) 
   } else {
     return fail(ALTO_EINVAL, "key_bits must be 0, 64 or 128 (got %d)", key_bits);
   }
+  // stored key width: the fewest 32-bit words that hold the index (1..4),
+  // unless key_bits forces the full 64- or 128-bit word
+  if (key_bits == 0) {
+    L.CW = next > 0 ? (next + 31) / 32 : 1;
+    if (L.CW > 2 * L.KW) L.CW = 2 * L.KW;
+  } else {
+    L.CW = 2 * L.KW;
+  }
   *out = L;
   return ALTO_OK;
 }
@@ -96,7 +104,7 @@ alto_status make_layout(int N, const uint64_t* dims, int key_bits, Layout* out) 
 void make_decode(const Layout& lay, const int* slot_mode, DecodeParams* dp) {
   std::memset(dp, 0, sizeof(*dp));
   dp->nmodes = lay.N;
-  dp->words32 = 2 * lay.KW;
+  dp->words32 = lay.CW;
   for (int s = 0; s < lay.N; ++s) {
     const int n = slot_mode[s];
     dp->mode_of[s] = n;

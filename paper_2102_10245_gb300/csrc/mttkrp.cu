@@ -97,7 +97,7 @@ void fill_launch(const alto_tensor_s* t, int mode, const void* const* factors, i
     if (m != mode) slot_mode[k++] = m;
   slot_mode[k] = mode;
   make_decode(lay, slot_mode, &l->args.dp);
-  l->args.keys = t->keys;
+  l->args.keys = t->ckeys;
   l->args.vals = t->vals;
   l->args.vbf16 = t->vdtype == ALTO_BF16 ? 1 : 0;
   l->args.M = t->M;
@@ -108,7 +108,7 @@ void fill_launch(const alto_tensor_s* t, int mode, const void* const* factors, i
   l->args.out_mode = mode;
   l->args.ivl = t->ivl;
   l->N = N;
-  l->KW = lay.KW;
+  l->W32 = lay.CW;
   l->sms = device_sms();
 }
 

@@ -1,0 +1,16 @@
+// Instantiation of the MTTKRP kernel family for BF16 factors and 64-bit stored
+// keys (2 32-bit words); one translation unit per (factor type, key width) so
+// that the kernel families compile in parallel.
+#include "mttkrp_kernels.cuh"
+
+namespace alto {
+
+cudaError_t mttkrp_dispatch_bf16_w2(const MttkrpLaunch& l, cudaStream_t s) {
+  return mttkrp_dispatch_typed<__nv_bfloat16, 2>(l, s);
+}
+
+cudaError_t mttkrp_batch_dispatch_bf16_w2(const BatchLaunch& l, cudaStream_t s) {
+  return mttkrp_batch_dispatch_typed<__nv_bfloat16, 2>(l, s);
+}
+
+}  // namespace alto

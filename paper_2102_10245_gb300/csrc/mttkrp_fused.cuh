@@ -300,16 +300,17 @@ __device__ __forceinline__ void fused_compute(GroupWork<N, R, FT>& w,
   fused_flush<FC>(FULL || p0 < cnt, fused_dst<AGG, R>(w.row[P - 1], outc, hotc), acc);
 }
 
-// One thread-block unit (8 consecutive segments) with the fused body; POL is
-// kAtomic or kWarpAgg.  All threads of the block call it together.  Each
-// warp walks its chunks as a two-stage pipeline: the gathers of chunk c are
-// issued, then chunk c+1 is loaded, de-linearized, grouped by output row and
-// staged (into the other half of the warp's double staging buffer) while
-// they are in flight, then chunk c is summed and flushed.
-template <int N, int KW, int R, typename FT, int POL>
-__device__ __forceinline__ void process_unit_fused(const MttkrpArgs& a, int64_t u,
-                                                   const BlockState<typename FTraits<FT>::AT>& st,
-                                                   uint4 (*s_stage)[kWarps][32][Stage<N, typename FTraits<FT>::VT>::W4]) {
+// Thread-block units u0, u0 + ustride, ... (below uend) of one MTTKRP with the
+// fused body; POL is kAtomic or kWarpAgg.  All threads of the block call it
+// together.  Each warp walks its chunks (chunks w, w+8, ... of every unit) as
+// one two-stage pipeline that runs on across unit boundaries: the gathers of
+// chunk c are issued, then chunk c+1 is loaded, de-linearized, grouped by
+// output row and staged (into the other half of the warp's double staging
+// buffer) while they are in flight, then chunk c is summed and flushed.
+template <int N, int W32, int R, typename FT, int POL>
+__device__ __forceinline__ void process_units_fused(const MttkrpArgs& a, int64_t u0, int64_t ustride, int64_t uend,
+                                                    const BlockState<typename FTraits<FT>::AT>& st,
+                                                    uint4 (*s_stage)[kWarps][32][Stage<N, typename FTraits<FT>::VT>::W4]) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
   using FC = FCols<R, FT>;
@@ -325,22 +326,40 @@ __device__ __forceinline__ void process_unit_fused(const MttkrpArgs& a, int64_t 
   const char* fb[NR];
 #pragma unroll
   for (int s = 0; s < NR; ++s) fb[s] = static_cast<const char*>(a.f[s]) + c * FC::BB;
-
-  const int64_t useg1 = (u + 1) * kUnitSegs < a.L ? (u + 1) * kUnitSegs : a.L;
-  const int64_t ub = seg_begin(u * kUnitSegs, a.M, a.L), ue = seg_begin(useg1, a.M, a.L);
   constexpr int64_t kStep = kWarps * 32;
 
-  // decode, group and stage the chunk at `base` (key k, value v of this lane)
+  // a chunk of this warp: unit u, first nonzero base, end of the unit ue
+  // (u >= uend marks the end of the walk)
+  struct Cur {
+    int64_t u, base, ue;
+  };
+  auto first_in = [&](int64_t u) -> Cur {
+    for (; u < uend; u += ustride) {
+      const int64_t useg1 = (u + 1) * kUnitSegs < a.L ? (u + 1) * kUnitSegs : a.L;
+      const int64_t ub = seg_begin(u * kUnitSegs, a.M, a.L), ue = seg_begin(useg1, a.M, a.L);
+      const int64_t base = ub + static_cast<int64_t>(warp) * 32;
+      if (base < ue) return Cur{u, base, ue};
+    }
+    return Cur{uend, 0, 0};
+  };
+  auto next = [&](Cur x) -> Cur {
+    x.base += kStep;
+    return x.base < x.ue ? x : first_in(x.u + ustride);
+  };
+
+  using VR = typename VRaw<VT>::T;
+  // decode, group and stage chunk x (key k, raw value word vr of this lane)
   // into buffer b; returns its nonzero count
-  auto front = [&](int64_t base, const KeyT<KW>& k, VT v, int b) -> int {
-    const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
+  auto front = [&](const Cur& x, const CKey<W32>& k, VR vr, int b) -> int {
+    const int cnt = static_cast<int>(x.ue - x.base < 32 ? x.ue - x.base : 32);
     const bool ok = lane < cnt;
+    const VT v = value_of<VT>(a, vr, x.base + lane);
     uint32_t id[N];
 #pragma unroll
-    for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
+    for (int s = 0; s < N; ++s) id[s] = extract_c<W32>(k, a.dp, s);
     int pos = lane;
     if constexpr (AGG) {
-      if (H > 0 && ok && (a.hot_key_bit < 0 || key_bit<KW>(k, a.hot_key_bit))) {
+      if (H > 0 && ok && (a.hot_key_bit < 0 || ckey_bit<W32>(k, a.hot_key_bit))) {
         const int slot = hot_lookup(st.hkeys, st.hidx, id[N - 1], a.hot_bits);
         if (slot >= 0) id[N - 1] = 0x80000000u | static_cast<uint32_t>(slot);
       }
@@ -362,44 +381,47 @@ __device__ __forceinline__ void process_unit_fused(const MttkrpArgs& a, int64_t 
     if (ok) stage_store<N, VT>(s_stage[b][warp][pos], id, v);
     return cnt;
   };
-  auto load = [&](int64_t x, KeyT<KW>& k, VT& v) {
-    if (x + lane < ue) {
-      k = load_key<KW>(a.keys, x + lane);
-      v = load_value<VT>(a, x + lane);
+  auto load = [&](const Cur& x, CKey<W32>& k, VR& v) {
+    if (x.u < uend && x.base + lane < x.ue) {
+      k = load_ckey<W32>(a.keys, x.base + lane);
+      v = load_value_raw<VT>(a, x.base + lane);
     }
   };
 
-  int64_t base = ub + static_cast<int64_t>(warp) * 32;
-  if (base >= ue) return;
-  KeyT<KW> kc{}, kn{};
-  VT vc = VT(0), vn = VT(0);
-  load(base, kc, vc);
-  load(base + kStep, kn, vn);
+  Cur cc = first_in(u0);
+  if (cc.u >= uend) return;
+  Cur c1 = next(cc);
+  CKey<W32> kc{}, kn{};
+  VR vc{}, vn{};
+  load(cc, kc, vc);
+  load(c1, kn, vn);
   int buf = 0;
-  int cnt = front(base, kc, vc, buf);
+  int cnt = front(cc, kc, vc, buf);
   __syncwarp();
   GroupWork<N, R, FT> w;
   if (cnt == 32)
     fused_prologue<N, R, FT, true>(w, s_stage[buf][warp], p0, cnt, fb);
   else
     fused_prologue<N, R, FT, false>(w, s_stage[buf][warp], p0, cnt, fb);
-  for (; base < ue; base += kStep) {
-    const int64_t nb = base + kStep;
+  while (true) {
+    const Cur cn = c1;  // the chunk after cc
     int cnt_n = 0;
-    if (nb < ue) {  // warp-uniform
+    if (cn.u < uend) {  // warp-uniform
       kc = kn;
       vc = vn;
-      load(nb + kStep, kn, vn);
-      cnt_n = front(nb, kc, vc, buf ^ 1);
+      c1 = next(cn);
+      load(c1, kn, vn);
+      cnt_n = front(cn, kc, vc, buf ^ 1);
     }
     if (cnt == 32)
       fused_compute<N, R, FT, AGG, true>(w, s_stage[buf][warp], p0, cnt, fb, outc, hotc);
     else
       fused_compute<N, R, FT, AGG, false>(w, s_stage[buf][warp], p0, cnt, fb, outc, hotc);
     __syncwarp();
+    if (cn.u >= uend) break;
     if (cnt_n == 32)
       fused_prologue<N, R, FT, true>(w, s_stage[buf ^ 1][warp], p0, cnt_n, fb);
-    else if (cnt_n > 0)
+    else
       fused_prologue<N, R, FT, false>(w, s_stage[buf ^ 1][warp], p0, cnt_n, fb);
     cnt = cnt_n;
     buf ^= 1;

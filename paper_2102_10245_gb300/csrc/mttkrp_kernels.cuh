@@ -211,7 +211,7 @@ __device__ __forceinline__ void red_vec(double* out, const double* v) {
 }
 
 struct MttkrpArgs {
-  const uint64_t* keys;
+  const uint32_t* keys;      // stored keys, W32 words each
   const void* vals;          // FP64 when the factors are FP64, else FP32 or BF16 (vbf16)
   int64_t M;
   int64_t L;                 // line segments
@@ -263,18 +263,49 @@ static_assert(sizeof(MttkrpArgs) % 4 == 0, "MttkrpArgs is copied as 32-bit words
 
 // Value x of the tensor as the accumulation's value type: FP64 values for
 // FP64 factors; FP32 or BF16 values (widened exactly) otherwise.  Streamed
-// once, so loaded with the evict-first hint.
+// once, so loaded with the evict-first hint.  Both 32-bit forms take one
+// 4-byte load and no branch: FP32 reads word x; BF16 reads word x/2, whose
+// low half holds the even element and high half the odd one.  The load and
+// the widening are separate steps: a pipeline that prefetches the next
+// chunk's values keeps the raw word and widens it when the chunk is used, so
+// the load's latency stays hidden (widening right after the load made every
+// prefetch wait for its data: 4.08 against 3.42 ms per mode).  The value
+// buffer is padded past M, so the word of the last odd-count BF16 element is
+// in bounds.
 template <typename VT>
-__device__ __forceinline__ VT load_value(const MttkrpArgs& a, int64_t x) {
+struct VRaw {
+  using T = uint32_t;
+};
+template <>
+struct VRaw<double> {
+  using T = double;
+};
+
+template <typename VT>
+__device__ __forceinline__ typename VRaw<VT>::T load_value_raw(const MttkrpArgs& a, int64_t x) {
   if constexpr (std::is_same_v<VT, double>) {
     return __ldcs(static_cast<const double*>(a.vals) + x);
   } else {
-    if (a.vbf16) {
-      const unsigned short b = __ldcs(static_cast<const unsigned short*>(a.vals) + x);
-      return __uint_as_float(static_cast<uint32_t>(b) << 16);
-    }
-    return __ldcs(static_cast<const float*>(a.vals) + x);
+    return __ldcs(static_cast<const unsigned int*>(a.vals) + (x >> a.vbf16));
   }
+}
+
+template <typename VT>
+__device__ __forceinline__ VT value_of(const MttkrpArgs& a, typename VRaw<VT>::T w, int64_t x) {
+  if constexpr (std::is_same_v<VT, double>) {
+    return w;
+  } else {
+    const uint32_t h = static_cast<uint32_t>(a.vbf16);  // 0 or 1
+    const uint32_t odd = static_cast<uint32_t>(x) & h;
+    const uint32_t lsh = (h & ~odd) << 4;      // 16 for an even BF16 element
+    const uint32_t keep = ~(odd * 0xffffu);    // 0xffff0000 for an odd one
+    return __uint_as_float((w << lsh) & keep);
+  }
+}
+
+template <typename VT>
+__device__ __forceinline__ VT load_value(const MttkrpArgs& a, int64_t x) {
+  return value_of<VT>(a, load_value_raw<VT>(a, x), x);
 }
 
 // staged tuple: N indices and the value, padded to 16-byte words
@@ -482,7 +513,7 @@ __device__ __forceinline__ BlockState<AT> hot_table(const MttkrpArgs& a, unsigne
 
 // One thread-block unit (8 consecutive segments) of one MTTKRP.  All threads
 // of the block call it together.
-template <int N, int KW, int R, typename FT, int POL>
+template <int N, int W32, int R, typename FT, int POL>
 __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
                                              const BlockState<typename FTraits<FT>::AT>& st,
                                              uint4 (*s_stage)[32][Stage<N, typename FTraits<FT>::VT>::W4],
@@ -548,30 +579,31 @@ __device__ __forceinline__ void process_unit(const MttkrpArgs& a, int64_t u,
 
   // chunks of this unit: warp w takes w, w + 8, ...
   int64_t base = ub + static_cast<int64_t>(warp) * 32;
-  KeyT<KW> kn{};
-  VT vn = VT(0);
+  CKey<W32> kn{};
+  typename VRaw<VT>::T vn{};
   if (base + lane < ue) {
-    kn = load_key<KW>(a.keys, base + lane);
-    vn = load_value<VT>(a, base + lane);
+    kn = load_ckey<W32>(a.keys, base + lane);
+    vn = load_value_raw<VT>(a, base + lane);
   }
   for (; base < ue; base += kWarps * 32) {
     const int cnt = static_cast<int>(ue - base < 32 ? ue - base : 32);
     const bool ok = lane < cnt;
-    const KeyT<KW> k = kn;
-    const VT v = vn;
+    const CKey<W32> k = kn;
+    const typename VRaw<VT>::T vraw = vn;
     const int64_t nb = base + kWarps * 32;
     if (nb + lane < ue) {  // prefetch the warp's next chunk
-      kn = load_key<KW>(a.keys, nb + lane);
-      vn = load_value<VT>(a, nb + lane);
+      kn = load_ckey<W32>(a.keys, nb + lane);
+      vn = load_value_raw<VT>(a, nb + lane);
     }
+    const VT v = value_of<VT>(a, vraw, base + lane);
     uint32_t id[N];
 #pragma unroll
-    for (int s = 0; s < N; ++s) id[s] = extract<KW>(k, a.dp, s);
+    for (int s = 0; s < N; ++s) id[s] = extract_c<W32>(k, a.dp, s);
     if constexpr (POL == kWarpAgg) {
       // hot rows are staged as (bit 31 | table slot); the host enables the
       // table only when every output row is below 2^31.  Only nonzeros
       // whose key carries the hot-row flag probe the table.
-      if (H > 0 && ok && (a.hot_key_bit < 0 || key_bit<KW>(k, a.hot_key_bit))) {
+      if (H > 0 && ok && (a.hot_key_bit < 0 || ckey_bit<W32>(k, a.hot_key_bit))) {
         const int slot = hot_lookup(st.hkeys, st.hidx, id[N - 1], a.hot_bits);
         if (slot >= 0) id[N - 1] = 0x80000000u | static_cast<uint32_t>(slot);
       }
@@ -703,7 +735,7 @@ namespace alto {
 #endif
 constexpr int kFusedBlocks = ALTO_FUSED_BLOCKS;
 
-template <int N, int KW, int R, typename FT, int POL, bool FUSED = false>
+template <int N, int W32, int R, typename FT, int POL, bool FUSED = false>
 __global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
@@ -714,11 +746,11 @@ __global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_ker
   BlockState<AT> st{0, nullptr, nullptr, nullptr};
   if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(a, dyn, blockIdx.x % kHotReplicas);
   const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    if constexpr (FUSED && (POL == kAtomic || POL == kWarpAgg))
-      process_unit_fused<N, KW, R, FT, POL>(a, u, st, s_stage2);
-    else
-      process_unit<N, KW, R, FT, POL>(a, u, st, s_stage, s_lorows, dyn);
+  if constexpr (FUSED && (POL == kAtomic || POL == kWarpAgg)) {
+    process_units_fused<N, W32, R, FT, POL>(a, blockIdx.x, gridDim.x, units, st, s_stage2);
+  } else {
+    for (int64_t u = blockIdx.x; u < units; u += gridDim.x)
+      process_unit<N, W32, R, FT, POL>(a, u, st, s_stage, s_lorows, dyn);
   }
 }
 
@@ -734,7 +766,7 @@ struct BatchArgs {
   int hot_replicas;            // copies of each item's hot rows
 };
 
-template <int N, int KW, int R, typename FT, int POL, bool FUSED = false>
+template <int N, int W32, int R, typename FT, int POL, bool FUSED = false>
 __global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_batch_kernel(const __grid_constant__ BatchArgs b) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
@@ -769,9 +801,10 @@ __global__ void __launch_bounds__(kThreads, FUSED ? kFusedBlocks : 4) mttkrp_bat
       if constexpr (POL == kWarpAgg) st = hot_table<AT, R>(s_args, dyn, blockIdx.x % b.hot_replicas);
     }
     if constexpr (FUSED && (POL == kAtomic || POL == kWarpAgg))
-      process_unit_fused<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage2);
+      process_units_fused<N, W32, R, FT, POL>(s_args, gu - b.unit_prefix[item], 1, gu - b.unit_prefix[item] + 1,
+                                              st, s_stage2);
     else
-      process_unit<N, KW, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage, s_lorows, dyn);
+      process_unit<N, W32, R, FT, POL>(s_args, gu - b.unit_prefix[item], st, s_stage, s_lorows, dyn);
   }
 }
 
@@ -825,7 +858,7 @@ __global__ void __launch_bounds__(256) hot_reduce_batch_kernel(const HotItem* __
 
 // Any order (runtime N <= kMaxModes) and any rank: one warp per segment,
 // lanes stride over the rank, scalar atomics.
-template <int KW, typename FT>
+template <int W32, typename FT>
 __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_constant__ MttkrpArgs a) {
   using AT = typename FTraits<FT>::AT;
   using VT = typename FTraits<FT>::VT;
@@ -840,8 +873,8 @@ __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_c
     for (int64_t base = s0; base < s1; base += 32) {
       const int cnt = static_cast<int>(s1 - base < 32 ? s1 - base : 32);
       if (lane < cnt) {
-        const KeyT<KW> k = load_key<KW>(a.keys, base + lane);
-        for (int s = 0; s < Nm; ++s) s_idx[warp][s][lane] = extract<KW>(k, a.dp, s);
+        const CKey<W32> k = load_ckey<W32>(a.keys, base + lane);
+        for (int s = 0; s < Nm; ++s) s_idx[warp][s][lane] = extract_c<W32>(k, a.dp, s);
         s_val[warp][lane] = load_value<VT>(a, base + lane);
       }
       __syncwarp();
@@ -866,7 +899,7 @@ __global__ void __launch_bounds__(kThreads) mttkrp_generic_kernel(const __grid_c
 struct MttkrpLaunch {
   MttkrpArgs args;
   int N;
-  int KW;
+  int W32;
   int variant;   // ATOMIC / WARPAGG / SMEM / TEMP (the generic kernel ignores it)
   int sms;       // SM count of the device
   size_t smem_dyn;
@@ -874,18 +907,29 @@ struct MttkrpLaunch {
   bool generic;  // the rank- and order-generic kernel whatever the shape
 };
 
-cudaError_t mttkrp_dispatch_f32_k1(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_f32_k2(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_f64_k1(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_f64_k2(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_bf16_k1(const MttkrpLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_dispatch_bf16_k2(const MttkrpLaunch& l, cudaStream_t s);
+// per factor type and stored key width (W32 32-bit words), one translation unit each
+#define ALTO_DECLARE_DISPATCH(T, WW)                                                        \
+  cudaError_t mttkrp_dispatch_##T##_w##WW(const MttkrpLaunch& l, cudaStream_t s);           \
+  cudaError_t mttkrp_batch_dispatch_##T##_w##WW(const struct BatchLaunch& l, cudaStream_t s);
+ALTO_DECLARE_DISPATCH(f32, 1)
+ALTO_DECLARE_DISPATCH(f32, 2)
+ALTO_DECLARE_DISPATCH(f32, 3)
+ALTO_DECLARE_DISPATCH(f32, 4)
+ALTO_DECLARE_DISPATCH(f64, 1)
+ALTO_DECLARE_DISPATCH(f64, 2)
+ALTO_DECLARE_DISPATCH(f64, 3)
+ALTO_DECLARE_DISPATCH(f64, 4)
+ALTO_DECLARE_DISPATCH(bf16, 1)
+ALTO_DECLARE_DISPATCH(bf16, 2)
+ALTO_DECLARE_DISPATCH(bf16, 3)
+ALTO_DECLARE_DISPATCH(bf16, 4)
+#undef ALTO_DECLARE_DISPATCH
 
 // launch description of one group of the batched entry point
 struct BatchLaunch {
   BatchArgs args;
   int N;
-  int KW;
+  int W32;
   int R;
   int variant;   // ATOMIC / WARPAGG / SMEM
   int sms;
@@ -894,18 +938,19 @@ struct BatchLaunch {
   bool fused;     // ATOMIC / WARPAGG through the fused body
 };
 
-cudaError_t mttkrp_batch_dispatch_f32_k1(const BatchLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_batch_dispatch_f32_k2(const BatchLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_batch_dispatch_f64_k1(const BatchLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_batch_dispatch_f64_k2(const BatchLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_batch_dispatch_bf16_k1(const BatchLaunch& l, cudaStream_t s);
-cudaError_t mttkrp_batch_dispatch_bf16_k2(const BatchLaunch& l, cudaStream_t s);
+#define ALTO_PICK_W(T, KIND, L, S)                                     \
+  switch ((L).W32) {                                                   \
+    case 1: return mttkrp_##KIND##dispatch_##T##_w1(L, S);             \
+    case 2: return mttkrp_##KIND##dispatch_##T##_w2(L, S);             \
+    case 3: return mttkrp_##KIND##dispatch_##T##_w3(L, S);             \
+    default: return mttkrp_##KIND##dispatch_##T##_w4(L, S);            \
+  }
 
 inline cudaError_t mttkrp_batch_dispatch(const BatchLaunch& l, alto_dtype fdtype, cudaStream_t s) {
   switch (fdtype) {
-    case ALTO_F64: return l.KW == 1 ? mttkrp_batch_dispatch_f64_k1(l, s) : mttkrp_batch_dispatch_f64_k2(l, s);
-    case ALTO_F32: return l.KW == 1 ? mttkrp_batch_dispatch_f32_k1(l, s) : mttkrp_batch_dispatch_f32_k2(l, s);
-    default: return l.KW == 1 ? mttkrp_batch_dispatch_bf16_k1(l, s) : mttkrp_batch_dispatch_bf16_k2(l, s);
+    case ALTO_F64: ALTO_PICK_W(f64, batch_, l, s)
+    case ALTO_F32: ALTO_PICK_W(f32, batch_, l, s)
+    default: ALTO_PICK_W(bf16, batch_, l, s)
   }
 }
 
@@ -932,18 +977,18 @@ cudaError_t launch_batch(Kern kern, const BatchLaunch& l, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename FT, int KW>
+template <typename FT, int W32>
 cudaError_t mttkrp_batch_dispatch_typed(const BatchLaunch& l, cudaStream_t s) {
 #define ALTO_BLAUNCH_NR(NN, RR)                                                                  \
   do {                                                                                           \
     switch (l.variant) {                                                                         \
-      case kSmem: return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kSmem>, l, s);          \
+      case kSmem: return launch_batch(mttkrp_batch_kernel<NN, W32, RR, FT, kSmem>, l, s);          \
       case kAtomic:                                                                              \
-        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic, true>, l, s); \
-        return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kAtomic>, l, s);                  \
+        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, W32, RR, FT, kAtomic, true>, l, s); \
+        return launch_batch(mttkrp_batch_kernel<NN, W32, RR, FT, kAtomic>, l, s);                  \
       default:                                                                                   \
-        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg, true>, l, s); \
-        return launch_batch(mttkrp_batch_kernel<NN, KW, RR, FT, kWarpAgg>, l, s);                 \
+        if (l.fused) return launch_batch(mttkrp_batch_kernel<NN, W32, RR, FT, kWarpAgg, true>, l, s); \
+        return launch_batch(mttkrp_batch_kernel<NN, W32, RR, FT, kWarpAgg>, l, s);                 \
     }                                                                                            \
   } while (0)
 #define ALTO_BLAUNCH_R(NN)              \
@@ -970,9 +1015,9 @@ cudaError_t mttkrp_batch_dispatch_typed(const BatchLaunch& l, cudaStream_t s) {
 
 inline cudaError_t mttkrp_dispatch(const MttkrpLaunch& l, alto_dtype fdtype, cudaStream_t s) {
   switch (fdtype) {
-    case ALTO_F64: return l.KW == 1 ? mttkrp_dispatch_f64_k1(l, s) : mttkrp_dispatch_f64_k2(l, s);
-    case ALTO_F32: return l.KW == 1 ? mttkrp_dispatch_f32_k1(l, s) : mttkrp_dispatch_f32_k2(l, s);
-    default: return l.KW == 1 ? mttkrp_dispatch_bf16_k1(l, s) : mttkrp_dispatch_bf16_k2(l, s);
+    case ALTO_F64: ALTO_PICK_W(f64, , l, s)
+    case ALTO_F32: ALTO_PICK_W(f32, , l, s)
+    default: ALTO_PICK_W(bf16, , l, s)
   }
 }
 
@@ -998,22 +1043,22 @@ cudaError_t launch_persistent(Kern kern, const MttkrpLaunch& l, size_t smem, int
 }
 
 // Instantiate and launch for one factor type and key width.
-template <typename FT, int KW>
+template <typename FT, int W32>
 cudaError_t mttkrp_dispatch_typed(const MttkrpLaunch& l, cudaStream_t s) {
   const MttkrpArgs& a = l.args;
   const int64_t units = (a.L + kUnitSegs - 1) / kUnitSegs;
-  if (l.generic) return launch_persistent(mttkrp_generic_kernel<KW, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
+  if (l.generic) return launch_persistent(mttkrp_generic_kernel<W32, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
 #define ALTO_LAUNCH_NR(NN, RR)                                                                           \
   do {                                                                                                   \
     switch (l.variant) {                                                                                 \
-      case kSmem: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kSmem>, l, l.smem_dyn, units, s); \
-      case kTemp: return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kTemp>, l, 0, units, s);        \
+      case kSmem: return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kSmem>, l, l.smem_dyn, units, s); \
+      case kTemp: return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kTemp>, l, 0, units, s);        \
       case kWarpAgg:                                                                                     \
-        if (l.fused) return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg, true>, l, l.smem_dyn, units, s); \
-        return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kWarpAgg>, l, l.smem_dyn, units, s);    \
+        if (l.fused) return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kWarpAgg, true>, l, l.smem_dyn, units, s); \
+        return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kWarpAgg>, l, l.smem_dyn, units, s);    \
       default:                                                                                           \
-        if (l.fused) return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic, true>, l, 0, units, s); \
-        return launch_persistent(mttkrp_kernel<NN, KW, RR, FT, kAtomic>, l, 0, units, s);              \
+        if (l.fused) return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kAtomic, true>, l, 0, units, s); \
+        return launch_persistent(mttkrp_kernel<NN, W32, RR, FT, kAtomic>, l, 0, units, s);              \
     }                                                                                                    \
   } while (0)
 #define ALTO_LAUNCH_R(NN)              \
@@ -1035,7 +1080,7 @@ cudaError_t mttkrp_dispatch_typed(const MttkrpLaunch& l, cudaStream_t s) {
   }
 #undef ALTO_LAUNCH_R
 #undef ALTO_LAUNCH_NR
-  return launch_persistent(mttkrp_generic_kernel<KW, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
+  return launch_persistent(mttkrp_generic_kernel<W32, FT>, l, 0, (a.L + kWarps - 1) / kWarps, s);
 }
 
 // Whether the specialised kernels cover (N, R); otherwise the generic one runs.

@@ -14,8 +14,6 @@
 // libalto keeps until the process exits.  All calls share it: two calls whose
 // work overlaps on the GPU (different streams, or different host threads on
 // one device) race on it and must be serialised by the caller.
-#include <mutex>
-
 #include "internal.h"
 
 namespace alto {
@@ -34,27 +32,15 @@ constexpr size_t kScratchWords = kKeyAltWords + kPermAltWords + kSortWords + kSt
 
 __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
-std::mutex g_setup_mutex;
-void* g_scratch_addr[64] = {};
-
-// Device address of the scratch array for the current device.  The array's
-// name in host code only stands in for the symbol; the address the kernels
-// need is looked up once per device (the first call on that device) and kept
-// for the life of the process, so a caller that resets the device
-// (cudaDeviceReset) must not call this entry point afterwards.
+// Device address of the scratch array in the current context.  The array's
+// name in host code only stands in for the symbol; the address is looked up
+// on every call (cheap once the module is loaded), so a context that was torn
+// down and re-created (cudaDeviceReset) gets the new array, not a stale one.
 alto_status scratch_for_current_device(unsigned long long** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(ALTO_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return fail(ALTO_EINVAL, "device ordinal %d not supported", dev);
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_addr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return fail(ALTO_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_scratch_addr[dev] = p;
-  }
-  *out = static_cast<unsigned long long*>(g_scratch_addr[dev]);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return fail(ALTO_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  *out = static_cast<unsigned long long*>(p);
   return ALTO_OK;
 }
 

@@ -488,3 +488,75 @@ def test_sampled_mttkrp_equals_full_rows():
         rows = np.sort(rng.choice(dims[n], size=500, replace=False))
         got = oracle.mttkrp_sampled(dims, idx, vals, lambda m, ids: U[m][ids], n, rows)
         assert np.array_equal(got, full[rows])
+
+
+# ---------------------------------------------------------------------------
+# transposition (Sec. 5: sorting the nonzeros by their coordinates in the new
+# mode order)
+
+
+def _transpose_bruteforce(dims, idx, modes):
+    """No sort: walk the chosen modes' coordinate tuples in lexicographic
+    order (itertools.product over their ranges) and list the nonzeros that
+    hold each tuple, those by ascending ALTO key, then input position."""
+    keys = oracle.encode(dims, idx)
+    by = {}
+    for x in range(len(idx[0])):
+        by.setdefault(tuple(int(idx[m][x]) for m in modes), []).append(x)
+    out = []
+    for t in itertools.product(*[range(dims[m]) for m in modes]):
+        out += sorted(by.get(t, []), key=lambda x: (int(keys[x, 1]), int(keys[x, 0]), x))
+    return np.array(out, dtype=np.int64)
+
+
+def _random_coo(dims, M, seed):
+    """Coordinates drawn with replacement (so duplicates occur)."""
+    rng = np.random.default_rng(seed)
+    return [rng.integers(0, d, M).astype(np.uint32) for d in dims]
+
+
+@pytest.mark.parametrize("dims,M", [((4, 8, 2), 40), ((5, 3, 7), 120), ((3, 4, 2, 5), 90), ((9,), 30)])
+def test_transpose_matches_bruteforce(dims, M):
+    idx = _random_coo(dims, M, sum(dims))
+    N = len(dims)
+    sels = [list(p) for p in itertools.permutations(range(N))]
+    sels += [[m] for m in range(N)] + [list(p) for p in itertools.permutations(range(N), 2)][:6]
+    for modes in sels:
+        order, src = oracle.transpose(dims, idx, modes)
+        assert np.array_equal(src, _transpose_bruteforce(dims, idx, modes)), modes
+        # order indexes ALTO order: the ALTO-ordered input positions under it
+        alto = oracle.sort_perm(oracle.encode(dims, idx))
+        assert np.array_equal(alto[order], src)
+
+
+def test_transpose_rejects_most_significant_first():
+    """Planted mistake: applying the stable per-mode sorts most significant
+    mode first (instead of last) breaks the lexicographic order."""
+    dims = (5, 3, 7)
+    idx = _random_coo(dims, 120, 15)
+    modes = [2, 0, 1]
+    alto = oracle.sort_perm(oracle.encode(dims, idx))
+    coords = np.stack([np.asarray(a, np.int64)[alto] for a in idx], 1)
+    order = np.arange(len(alto))
+    for m in modes:
+        order = order[np.argsort(coords[order, m], kind="stable")]
+    assert not np.array_equal(alto[order], _transpose_bruteforce(dims, idx, modes))
+
+
+def test_transpose_full_order_of_distinct_coordinates_is_unique():
+    """With distinct coordinates and every mode chosen, the result is the
+    unique strictly increasing lexicographic sequence, whatever the input
+    order."""
+    rng = np.random.default_rng(3)
+    dims = (50, 40, 30)
+    flat = rng.choice(50 * 40 * 30, size=5000, replace=False)
+    idx = [(flat // (40 * 30)).astype(np.uint32), ((flat // 30) % 40).astype(np.uint32),
+           (flat % 30).astype(np.uint32)]
+    for modes in ([0, 1, 2], [2, 0, 1], [1, 2, 0]):
+        _, src = oracle.transpose(dims, idx, modes)
+        c = np.stack([np.asarray(idx[m], np.int64)[src] for m in modes], 1)
+        lin = (c[:, 0] * dims[modes[1]] + c[:, 1]) * dims[modes[2]] + c[:, 2]
+        assert (np.diff(lin) > 0).all()
+        shuffled = rng.permutation(len(flat))
+        _, src2 = oracle.transpose(dims, [a[shuffled] for a in idx], modes)
+        assert np.array_equal(shuffled[src2], src)
