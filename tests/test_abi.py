@@ -93,3 +93,23 @@ def test_host_decode_matches_oracle(alto_lib, dims):
     kw = layout_for_dims(dims)[2]
     got = decode_host(dims, keys[:, :kw])
     assert (got.astype(np.int64) == coords).all()
+
+
+def test_argument_errors_need_no_gpu(alto_lib):
+    """Entry points reject bad arguments on the host, before any CUDA call:
+    a NULL tensor handle, an unknown Gram engine, a bad Gram shape, and the
+    tensor-core engine asked for FP32 factors or a rank it has no kernel for."""
+    import ctypes
+    L = alto_lib
+    modes = (ctypes.c_int * 1)(0)
+    assert L.alto_transpose(None, 1, modes, None, None, None, 8, None, None) == 1
+    assert L.alto_set_gram_engine(None, 0) == 1
+    dummy = ctypes.c_void_p(16)
+    G = ctypes.c_void_p(32)
+    assert L.alto_gram(dummy, 10, 32, 2, 7, G, None) == 1          # engine out of range
+    assert L.alto_gram(dummy, 10, 65, 2, 0, G, None) == 1          # R above 64
+    assert L.alto_gram(dummy, -1, 32, 2, 0, G, None) == 1          # negative length
+    assert L.alto_gram(dummy, 10, 32, 2, 0, None, None) == 1       # NULL output
+    assert L.alto_gram(None, 10, 32, 2, 0, G, None) == 1           # NULL factor
+    assert L.alto_gram(dummy, 10, 32, 1, 2, G, None) == 1          # tensor cores with FP32 factors
+    assert L.alto_gram(dummy, 10, 24, 2, 2, G, None) == 1          # tensor cores at R = 24
