@@ -97,16 +97,6 @@ __device__ __forceinline__ int tile_off(int m, int k) {
   return (m >> 3) * kSBO + (k >> 3) * kLBO + (m & 7) * 16 + (k & 7) * 2;
 }
 
-template <bool NORM>
-struct GRaw {  // BF16 U: one 16-byte group per slot
-  uint4 v[4];
-};
-template <>
-struct GRaw<true> {  // FP32 A (and Mt): two 16-byte halves per slot
-  float4 a[4][2];
-  float4 m[4][2];
-};
-
 // Warps 0..R/32: add accumulator rows m < R (tensor-memory lane m, columns
 // 0..R-1) into the FP64 sums gacc (each thread owns its row: no conflicts).
 __device__ __forceinline__ void flush_accumulator(uint32_t tmem, int R, double* gacc) {
@@ -179,42 +169,9 @@ __global__ void __launch_bounds__(kGT) gram_tc_kernel(const __grid_constant__ Gr
   double ipd = 0.0;
   bool ok = true;
   int it = 0;
-  // raw loads of a chunk: this thread's 8-column groups (BF16 U, or FP32 A
-  // and, on the fit's mode, Mt); the next chunk's are issued before this
-  // chunk is staged, so a block keeps two chunks of loads in flight
-  GRaw<NORM> cur, nxt;
-  auto fetch = [&](int64_t ch, GRaw<NORM>& r) {
-    const int64_t k0 = ch * kGK;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gi = threadIdx.x + q * kGT;
-      const int k = gi / CG, c = (gi - k * CG) * 8;
-      const int64_t row = k0 + k;
-      const bool in = gi < groups && row < g.I;
-      if constexpr (NORM) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.a[q][0] = r.a[q][1] = r.m[q][0] = r.m[q][1] = z;
-        if (in) {
-          const float4* a = reinterpret_cast<const float4*>(static_cast<const float*>(g.src) + row * R + c);
-          r.a[q][0] = a[0];
-          r.a[q][1] = a[1];
-          if (g.Mt != nullptr) {
-            const float4* m = reinterpret_cast<const float4*>(g.Mt + row * R + c);
-            r.m[q][0] = m[0];
-            r.m[q][1] = m[1];
-          }
-        }
-      } else {
-        r.v[q] = in ? __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(g.src) + row * R + c))
-                    : make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
-  };
-  if (static_cast<int64_t>(blockIdx.x) < nchunks) fetch(blockIdx.x, cur);
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++it) {
     const int buf = it & 1;
     const int64_t k0 = ch * kGK;
-    if (ch + gridDim.x < nchunks) fetch(ch + gridDim.x, nxt);
     if (it > 0 && it % kFlushChunks == 0) {
       // every MMA so far has completed once the last commit has: move the
       // FP32 accumulator into the FP64 sums and start it again
@@ -225,33 +182,34 @@ __global__ void __launch_bounds__(kGT) gram_tc_kernel(const __grid_constant__ Gr
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
     }
-    // BF16 groups of this chunk (NORM: normalised, rounded and stored as U,
-    // and the fit's inner product)
+    // load (and, for NORM, normalise, round and store) this thread's groups
     uint4 vals[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+      const int gi = threadIdx.x + q * kGT;
+      vals[q] = make_uint4(0u, 0u, 0u, 0u);
+      if (gi >= groups) continue;
+      const int k = gi / CG, c = (gi - k * CG) * 8;
+      const int64_t row = k0 + k;
+      if (row >= g.I) continue;
       if constexpr (NORM) {
-        const int gi = threadIdx.x + q * kGT;
-        const int k = gi / CG, c = (gi - k * CG) * 8;
-        const int64_t row = k0 + k;
-        vals[q] = make_uint4(0u, 0u, 0u, 0u);
-        if (gi >= groups || row >= g.I) continue;
-        const float xs[8] = {cur.a[q][0].x, cur.a[q][0].y, cur.a[q][0].z, cur.a[q][0].w,
-                             cur.a[q][1].x, cur.a[q][1].y, cur.a[q][1].z, cur.a[q][1].w};
+        const float* a = static_cast<const float*>(g.src) + row * R + c;
+        const float4 x0 = *reinterpret_cast<const float4*>(a);
+        const float4 x1 = *reinterpret_cast<const float4*>(a + 4);
+        const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         __nv_bfloat16 h[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(xs[e] * inv[c + e]);
         vals[q] = *reinterpret_cast<const uint4*>(h);
         *reinterpret_cast<uint4*>(g.U + row * R + c) = vals[q];
         if (g.Mt != nullptr) {
-          const float ms[8] = {cur.m[q][0].x, cur.m[q][0].y, cur.m[q][0].z, cur.m[q][0].w,
-                               cur.m[q][1].x, cur.m[q][1].y, cur.m[q][1].z, cur.m[q][1].w};
+          const float* mt = g.Mt + row * R + c;
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            ipd += static_cast<double>(__bfloat162float(h[e]) * ms[e]) * lam[c + e];
+            ipd += static_cast<double>(__bfloat162float(h[e]) * mt[e]) * lam[c + e];
         }
       } else {
-        vals[q] = cur.v[q];
+        vals[q] = __ldg(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(g.src) + row * R + c));
       }
     }
     // the tile is free once the MMAs of two chunks ago have completed
@@ -289,7 +247,6 @@ __global__ void __launch_bounds__(kGT) gram_tc_kernel(const __grid_constant__ Gr
                        smem_u32(&mbar[buf]))
                    : "memory");
     }
-    cur = nxt;
   }
   // the last commit covers every MMA of the block
   bool drained = true;
@@ -323,10 +280,7 @@ __global__ void __launch_bounds__(kGT) gram_tc_kernel(const __grid_constant__ Gr
   }
 }
 
-// One wave: as many blocks as fit on the SMs at once (registers, shared
-// memory, and 512 tensor-memory columns per SM), capped by the chunk count.
-template <bool NORM>
-unsigned gram_tc_grid(int64_t I, int R, size_t dyn) {
+unsigned gram_tc_grid(int64_t I) {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -334,13 +288,8 @@ unsigned gram_tc_grid(int64_t I, int R, size_t dyn) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, gram_tc_kernel<NORM>, kGT, dyn) != cudaSuccess || per < 1)
-    per = 1;
-  const int ncols = R <= 32 ? 32 : 64;
-  if (per > 512 / ncols) per = 512 / ncols;
   int64_t g = (I + kGK - 1) / kGK;
-  const int64_t cap = static_cast<int64_t>(sms) * per;
+  const int64_t cap = static_cast<int64_t>(sms) * 3;  // up to 3 blocks of ~66 KB shared memory per SM
   if (g > cap) g = cap;
   return static_cast<unsigned>(g < 1 ? 1 : g);
 }
@@ -360,7 +309,7 @@ cudaError_t launch_gram_bf16_tc(const __nv_bfloat16* U, int64_t I, int R, double
   a.status = status;
   const size_t dyn = sizeof(double) * R * R;
   cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-  gram_tc_kernel<false><<<gram_tc_grid<false>(I, R, dyn), kGT, dyn, s>>>(a);
+  gram_tc_kernel<false><<<gram_tc_grid(I), kGT, dyn, s>>>(a);
   note_launch();
   return cudaGetLastError();
 }
@@ -382,7 +331,7 @@ cudaError_t launch_normalize_gram_bf16_tc(const float* A, int64_t I, int R, cons
   a.ip = ip;
   const size_t dyn = sizeof(double) * R * R;
   cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(dyn));
-  gram_tc_kernel<true><<<gram_tc_grid<true>(I, R, dyn), kGT, dyn, s>>>(a);
+  gram_tc_kernel<true><<<gram_tc_grid(I), kGT, dyn, s>>>(a);
   note_launch();
   return cudaGetLastError();
 }
