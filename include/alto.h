@@ -416,9 +416,8 @@ alto_status alto_launch_count(uint64_t *count);
  * that array's device address in the current context.  All calls
  * share the array: calls that overlap on the GPU (other streams, other host
  * threads on the same device) race and must be serialised by the caller.
- * The call reads its status word back and synchronises `stream` at its end,
- * so it cannot run while the stream is being captured into a CUDA graph;
- * returns ALTO_ERANGE when an index is out of range.
+ * The call reads its status word back and synchronises `stream` at its end;
+ * it returns ALTO_ERANGE when an index is out of range.
  */
 #define ALTO_NOALLOC_MAX_NNZ 262144
 alto_status alto_linearize_noalloc(int nmodes, const uint64_t *dims,

@@ -7,7 +7,7 @@
 // another runtime (a cudaMalloc behind its back would break its accounting).
 // They still pass their own inputs and outputs; this entry point supplies the
 // sort's scratch itself.  The call reads its status word back and
-// synchronises the stream, so it cannot be recorded into a CUDA graph.
+// synchronises the stream before it returns.
 //
 // The array is kScratchWords 8-byte words (about 5.3 MB) of device memory
 // that every GPU which loads

@@ -4,8 +4,9 @@ Callers that cannot allocate device memory -- services that reserve all
 device memory up front, embedders whose allocator belongs to another runtime
 -- use this entry point.  Its keys and permutation must be the ALTO keys and
 the stable order that the oracle computes from the paper's definition (Sec.
-3.1), call after call, although every call reuses the same fixed scratch
-array, and a call must not allocate device memory.  The file is named so that
+3.1), and those alto_create gives for the same input, call after call, although
+every call reuses the same fixed scratch array, and a call must not allocate
+device memory.  The file is named so that
 pytest collects it last.
 """
 import ctypes
@@ -16,6 +17,7 @@ import torch
 
 import oracle
 import synth
+from helpers import make
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +68,17 @@ def test_noalloc_matches_oracle_on_two_calls(name, nnz):
         p = perm.cpu().numpy().view(np.uint32)
         assert (p == ref_perm).all()
         assert (k == ref_keys[ref_perm][:, :kw]).all()
+        # the existing entry point on the same input gives the same result:
+        # alto_create's keys (its helper-flag bits masked off) and permutation
+        at = make(dims, idx, vals)
+        ex, lay = at.export(), at.layout()
+        at.close()
+        ck = ex["keys"].copy()
+        for b in list(lay["flag_bit"]) + list(lay["hot_bit"]):
+            if b >= 0:
+                ck[:, b // 64] &= ~np.uint64(1 << (b % 64))
+        assert (p == ex["perm"]).all()
+        assert (k == ck).all()
 
 
 def test_noalloc_rejects_more_than_the_fixed_limit():
