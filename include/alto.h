@@ -242,7 +242,9 @@ alto_status alto_export(alto_t t, uint64_t *keys, uint32_t *perm, void *vals,
  * (overwritten).  `engine` is an alto_gram_engine; ALTO_GRAM_TENSOR_CORES
  * with FP32/FP64 factors or another R is ALTO_EINVAL.  Runs on `stream` and
  * synchronises it; ALTO_ETIMEOUT if a bounded device wait of the tensor-core
- * kernel ran out (G is then incomplete).
+ * kernel ran out (G is then incomplete).  All alto_gram calls share one
+ * device status word: calls that overlap on the GPU may report each other's
+ * timeout.
  */
 alto_status alto_gram(const void *U, int64_t I, int R, alto_dtype dtype,
                       int engine, double *G, void *stream);
